@@ -1,0 +1,364 @@
+"""Pins of the FP64 oracle against what the paper and textbook mathematics fix.
+
+Every test here checks the oracle against something other than itself: an algebraic
+property of the lattice, a closed form, a discrete identity the paper derives
+(Sec. 2.1), a coexistence solution from the EOS, or an exact conservation law.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import analytic as A
+from oracle import oracle as O
+from paper_2604_13407_gb300 import inputs as I
+from tests.setups import EPS_TC, SQRT2, cs_case, cs_params, s_q, vdw_params
+
+# ------------------------------------------------------------- lattice -----
+
+
+def test_lattice_tables_fixed_by_the_paper():
+    M, w, ex, ey, opp = O.tables()
+    # orthogonal rows with the Lallemand-Luo norms
+    assert np.array_equal(M @ M.T, np.diag([9, 36, 36, 6, 12, 6, 12, 4, 4]).astype(float))
+    # weights: isotropy conditions of D2Q9
+    assert math.isclose(w.sum(), 1.0, abs_tol=1e-15)
+    assert math.isclose(np.sum(w * ex * ex), 1.0 / 3.0, abs_tol=1e-15)
+    assert math.isclose(np.sum(w * ex**4), 1.0 / 3.0, abs_tol=1e-15)
+    assert math.isclose(np.sum(w * ex**2 * ey**2), 1.0 / 9.0, abs_tol=1e-15)
+    for i in range(9):
+        assert ex[opp[i]] == -ex[i] and ey[opp[i]] == -ey[i]
+    # rows are the moments the paper names: rho, j_x, j_y, p_xx, p_xy
+    assert np.array_equal(M[0], np.ones(9))
+    assert np.array_equal(M[3], ex) and np.array_equal(M[5], ey)
+    assert np.array_equal(M[7], ex**2 - ey**2) and np.array_equal(M[8], ex * ey)
+    # the sums used in Eq. (ali.2): e_1, e_5, e_8 have e_x = +1; e_3, e_6, e_7 have e_x = -1
+    assert sorted(np.nonzero(ex == 1)[0]) == [1, 5, 8]
+    assert sorted(np.nonzero(ex == -1)[0]) == [3, 6, 7]
+    assert sorted(np.nonzero(ey == 1)[0]) == [2, 5, 6]
+    # the sums used in Eq. (obl.1): rho u_beta ~ f_(1-4) + f_(2-3) + 2 f_(5-7)
+    ub = (ex + ey) / SQRT2
+    expect = np.zeros(9)
+    expect[[1, 2]] = 1
+    expect[[4, 3]] = -1
+    expect[5], expect[7] = 2, -2
+    assert np.allclose(ub, expect * SQRT2 / 2)
+
+
+def _textbook_feq(rho, ux, uy, ex, ey, w):
+    eu = ex * ux + ey * uy
+    return w * rho * (1 + 3 * eu + 4.5 * eu**2 - 1.5 * (ux * ux + uy * uy))
+
+
+def test_equilibrium_and_force_moments_are_textbook():
+    M, w, ex, ey, _ = O.tables()
+    p = cs_params()
+    rng = np.random.default_rng(1)
+    for _ in range(20):
+        f = rng.uniform(0.01, 0.1, 9)
+        out = O.collide_node(p, f, 0.3, rng.normal(size=2) * 1e-2, Fext=rng.normal(size=2) * 1e-4)
+        ux, uy = out["u"]
+        rho = f.sum()
+        # m_eq of Sec. 2 is M applied to the second-order Maxwellian equilibrium
+        assert np.allclose(M @ _textbook_feq(rho, ux, uy, ex, ey, w), out["meq"], rtol=0, atol=1e-15)
+        # F_m of Sec. 2 is M applied to Guo's forcing term w_i [3(e_i - u) + 9 (e_i.u) e_i].F
+        F = out["Fm"][[3, 5]]
+        eu = ex * ux + ey * uy
+        Fv = w * (3 * ((ex - ux) * F[0] + (ey - uy) * F[1]) + 9 * eu * (ex * F[0] + ey * F[1]))
+        assert np.allclose(M @ Fv, out["Fm"], rtol=0, atol=1e-16)
+
+
+def test_rest_equilibrium_is_weights_times_rho():
+    p = cs_params(nx=3, ny=2, periodic_x=True, periodic_y=True)
+    s = O.OracleSim(p)
+    rho = np.array([[0.1, 0.2, 0.3], [0.05, 0.33, 0.01]])
+    s.init(rho)
+    _, w, _, _, _ = O.tables()
+    A_ = s.get_state()
+    assert np.allclose(A_, w[:, None, None] * rho[None], rtol=1e-15, atol=0)
+
+
+# ------------------------------------------------------ EOS and force -----
+
+
+def test_psi_matches_eos_inversion():
+    for p in (cs_params(), vdw_params(1.0, 0.65)):
+        for rho in (0.005, 0.05, 0.2, 0.35):
+            if p.eos == 0:
+                rho *= 20
+            ref = A.psi(rho, p.eos, p.a, p.b, p.R, p.T, p.K_eos, p.G)
+            assert math.isclose(O.psi(p, rho), float(ref), rel_tol=1e-13)
+            assert math.isclose(O.p_eos(p, rho), float(A.p_eos(rho, p.eos, p.a, p.b, p.R, p.T, p.K_eos)), rel_tol=1e-13)
+
+
+def test_pairwise_force_closed_form_aligned():
+    ny = 24
+    p = cs_params(nx=1, ny=ny, periodic_x=True, periodic_y=True, G=-1.7)
+    s = O.OracleSim(p)
+    T, rg, rl = cs_case()
+    s.init(I.tanh_slab(1, ny, rl, rg, 10))
+    fl = s.fields()
+    psi_hat = math.sqrt(-p.G) * fl["psi"][:, 0]
+    ref = A.fint_closed_form(psi_hat)        # Eq. (obl.10), grid-aligned
+    assert np.allclose(fl["Finty"][:, 0], ref, rtol=0, atol=1e-15)
+    assert np.abs(fl["Fintx"]).max() == 0.0
+
+
+def test_pairwise_force_closed_form_oblique():
+    n = 24
+    p = cs_params(nx=n, ny=n, periodic_x=True, periodic_y=True, G=-0.6)
+    s = O.OracleSim(p)
+    T, rg, rl = cs_case()
+    s.init(I.oblique_slab(n, rl, rg, 10))
+    fl = s.fields()
+    prof = np.array([fl["psi"][0, i] for i in range(n)])   # node (x=i, y=0): alpha index i
+    ref = A.fint_closed_form(math.sqrt(-p.G) * prof, oblique=True)
+    Fx = np.array([fl["Fintx"][0, i] for i in range(n)])
+    Fy = np.array([fl["Finty"][0, i] for i in range(n)])
+    assert np.allclose(Fx, ref, rtol=0, atol=1e-15)
+    assert np.allclose(Fy, -ref, rtol=0, atol=1e-15)
+
+
+# ------------------------------------------------------- conservation -----
+
+
+def test_mass_conservation_to_roundoff():
+    T, rg, rl = cs_case()
+    p = cs_params(nx=4, ny=48, periodic_x=True, periodic_y=False, Fx=1e-6, scheme=1)
+    s = O.OracleSim(p)
+    s.init(I.tanh_slab(4, 48, rl, rg, 24))
+    m0 = s.diagnostics()[0]
+    s.step(3000)
+    m1 = s.diagnostics()[0]
+    assert abs(m1 - m0) / m0 < 1e-13
+
+
+def test_wall_momentum_balance_is_exact():
+    """Streaming from f_bar(n-1) to f(n): sum_x j(n) = sum_x j(n-1) + sum_x F(n-1) - D(n)
+    with D the momentum the bounce-back links hand to the walls."""
+    T, rg, rl = cs_case()
+    p = cs_params(nx=6, ny=40, periodic_x=True, periodic_y=False, Fx=2e-5, Fy=-1e-5, scheme=1)
+    s = O.OracleSim(p)
+    s.init(I.tanh_slab(6, 40, rl, rg, 20))
+    s.step(50)
+    for _ in range(4):
+        d0 = s.diagnostics()
+        s.step(1)
+        d1 = s.diagnostics()
+        for c in range(2):
+            lhs = d1[1 + c]
+            rhs = d0[1 + c] + d0[3 + c] - d1[5 + c]
+            assert abs(lhs - rhs) < 1e-15 * max(1.0, abs(d0[3 + c]) * 1e3)
+
+
+def test_interaction_strength_G_drops_out():
+    """psi ~ |G|^(-1/2), so F_int and |F_int|^2/(G psi^2) do not depend on G (Sec. 2)."""
+    T, rg, rl = cs_case()
+    res = []
+    for G in (-1.0, -2.7):
+        p = cs_params(nx=8, ny=24, periodic_x=True, periodic_y=True, G=G, Fx=1e-5)
+        s = O.OracleSim(p)
+        s.init(I.droplet(8, 24, rl, rg, 5, 3.5, 11.5, periodic_x=True))
+        s.step(300)
+        res.append(s.moments())
+    scale = np.abs(res[0][0]).max()
+    for a, b in zip(res[0], res[1]):
+        assert np.abs(a - b).max() < 1e-13 * scale
+
+
+# -------------------------------------------------- single-phase flows -----
+
+
+def _single_phase(ny, Lambda, steps, F=1e-6, rho0=0.3, tau=0.8):
+    p = cs_params(nx=1, ny=ny, periodic_x=True, periodic_y=False, Fx=F, rho_s=rho0,
+                  tau_l=tau, tau_g=tau, Lambda=Lambda)
+    s = O.OracleSim(p)
+    s.init(np.full((ny, 1), rho0))
+    s.step(steps)
+    return s, p
+
+
+def test_single_phase_poiseuille_exact_parabola():
+    """With Lambda = 3/16 (the TRT value that puts the bounce-back wall exactly half-way)
+    the steady profile is the parabola with walls at y = -1/2 and y = ny - 1/2."""
+    ny, rho0, F, tau = 16, 0.3, 1e-6, 0.8
+    s, p = _single_phase(ny, 3.0 / 16.0, 30000, F, rho0, tau)
+    rho, ux, uy = s.moments()
+    nu = (tau - 0.5) / 3.0
+    y = np.arange(ny)
+    exact = F / (2 * rho0 * nu) * (y + 0.5) * (ny - 0.5 - y)
+    assert np.abs(ux[:, 0] - exact).max() < 1e-10 * exact.max()
+    assert np.abs(uy).max() < 1e-12 * exact.max()
+
+
+def test_single_phase_second_difference():
+    """Eq. (fde.ali) for rho = const, F_int = 0, Q = 0: u'' = -F/(rho nu) at every interior node."""
+    ny, rho0, F, tau = 20, 0.3, 1e-6, 0.7
+    s, p = _single_phase(ny, 1.0 / 12.0, 30000, F, rho0, tau)
+    _, ux, _ = s.moments()
+    u = ux[:, 0]
+    nu = (tau - 0.5) / 3.0
+    d2 = u[:-2] + u[2:] - 2 * u[1:-1]
+    assert np.allclose(d2, -F / (rho0 * nu), rtol=1e-9, atol=0)
+
+
+def test_couette_moving_wall_exact():
+    ny, U, rho0 = 18, 1e-3, 0.3
+    solid = np.zeros((ny, 1), np.uint8)
+    solid[0] = solid[-1] = 1
+    wall_u = np.zeros((2, ny, 1))
+    wall_u[0, -1] = U
+    p = cs_params(nx=1, ny=ny, periodic_x=True, periodic_y=True, rho_s=rho0)
+    s = O.OracleSim(p, solid=solid, wall_u=wall_u)
+    s.init(np.full((ny, 1), rho0))
+    s.step(40000)
+    _, ux, _ = s.moments()
+    y = np.arange(1, ny - 1)
+    exact = U * (y - 0.5) / (ny - 2)
+    assert np.abs(ux[1:-1, 0] - exact).max() < 1e-10 * U
+
+
+# --------------------------------------------- two-phase aligned channel ---
+
+
+@pytest.fixture(scope="module")
+def aligned_steady():
+    """Two-phase Poiseuille between walls at y = -1/2 and y = ny - 1/2 (flow along x),
+    Carnahan-Starling at 0.7 T_c, epsilon = 1.895, both schemes at steady state."""
+    ny, F = 32, 1e-7
+    T, rg, rl = cs_case()
+    out = {}
+    for scheme in (0, 1):
+        p = cs_params(nx=1, ny=ny, periodic_x=True, periodic_y=False, Fx=F, scheme=scheme)
+        s = O.OracleSim(p)
+        s.init(I.tanh_slab(1, ny, rl, rg, ny / 2))
+        O.steady_state(s, 150000, rounds=4, settle=25000)
+        out[scheme] = (p, s.fields())
+    return out
+
+
+@pytest.mark.parametrize("scheme", [0, 1])
+def test_aligned_eq_ali3(aligned_steady, scheme):
+    p, fl = aligned_steady[scheme]
+    r = A.ali3_residual(fl["f"][1, :, 0], fl["f"][3, :, 0], fl["rho"][:, 0], fl["ux"][:, 0],
+                        p.Fx, fl["Q"][4, :, 0], s_q(p.tau_l))
+    scale = np.abs(fl["rho"][:, 0] * fl["ux"][:, 0]).max()
+    assert np.abs(r).max() < 1e-9 * scale
+
+
+@pytest.mark.parametrize("scheme", [0, 1])
+def test_aligned_fde(aligned_steady, scheme):
+    p, fl = aligned_steady[scheme]
+    nu = (p.tau_l - 0.5) / 3.0
+    r = A.fde_aligned_residual(fl["rho"][:, 0], fl["Finty"][:, 0], fl["ux"][:, 0], fl["Q"][4, :, 0], p.Fx, nu)
+    assert np.abs(r).max() < 1e-5 * p.Fx / nu
+
+
+@pytest.mark.parametrize("scheme", [0, 1])
+def test_aligned_eq_ali9_ali10_ali12(aligned_steady, scheme):
+    """Eqs. (ali.9), (ali.10), (ali.12) in the rotated frame (profile along y): they fix
+    the epsilon carried by Q_1 and Q_7 and hold for either Q_2 (Sec. 2.1.1)."""
+    p, fl = aligned_steady[scheme]
+    eps = p.epsilon
+    f = fl["f"][:, :, 0]
+    rho = fl["rho"][:, 0]
+    Fn = fl["Finty"][:, 0]
+    X = Fn**2 / (-p.G * fl["psi"][:, 0] ** 2)      # dt^2 F_hat^2 / psi_hat^2
+    tol = 1e-12
+    assert np.abs(f[0] + f[1] + f[3] - (2 / 3 * rho - eps / 8 * X)).max() < tol
+    assert np.abs(f[2] + f[5] + f[6] - (rho / 6 - Fn / 4 + eps / 16 * X)).max() < tol
+    assert np.abs(f[4] + f[7] + f[8] - (rho / 6 + Fn / 4 + eps / 16 * X)).max() < tol
+    lhs = rho[1:] - 1.5 * Fn[1:]
+    rhs = rho[:-1] + 1.5 * Fn[:-1] + 3 * eps / 8 * X[:-1] - 3 * eps / 8 * X[1:]
+    assert np.abs(lhs - rhs).max() < tol
+
+
+def test_aligned_improved_removes_oscillation_term(aligned_steady):
+    """Eq. (ali.final): the improved Q (Eq. qm6.ali in the aligned frame) cancels the third
+    term exactly, leaving a smooth finite-difference equation for u; the original scheme
+    keeps that term."""
+    def reduced(p, fl, with_third):
+        rho, Fn, u = fl["rho"][:, 0], fl["Finty"][:, 0], fl["ux"][:, 0]
+        X = Fn**2 / (-p.G * fl["psi"][:, 0] ** 2)
+        e = p.epsilon
+        nu = (p.tau_l - 0.5) / 3.0
+        d2 = u[:-2] + u[2:] - 2 * u[1:-1]
+        r = (rho[1:-1] + 3 * e / 8 * X[1:-1]) * d2 + 1.5 * Fn[1:-1] * (u[2:] - u[:-2])
+        if with_third:
+            r = r - 3 * e / 8 * (X[:-2] * u[:-2] + X[2:] * u[2:] - 2 * X[1:-1] * u[1:-1])
+        return np.abs(r + p.Fx / nu).max(), p.Fx / nu
+    p1, f1 = aligned_steady[1]
+    r_imp, scale = reduced(p1, f1, with_third=False)
+    assert r_imp < 1e-5 * scale
+    p0, f0 = aligned_steady[0]
+    r_orig_full, _ = reduced(p0, f0, with_third=True)
+    r_orig_reduced, _ = reduced(p0, f0, with_third=False)
+    assert r_orig_full < 1e-5 * scale
+    assert r_orig_reduced > 1e-2 * scale
+
+
+def test_aligned_err_improved_beats_original(aligned_steady):
+    """Sec. 3.1, Table 1: Err against Eq. (u.plane) integrated with the converged density
+    is much smaller for the improved scheme when epsilon > 0."""
+    errs = {}
+    for scheme in (0, 1):
+        p, fl = aligned_steady[scheme]
+        nu = lambda r: A.nu_of_rho(r, p.tau_l, p.tau_g, p.rho_l, p.rho_g)
+        th = A.poiseuille_theory(fl["rho"][:, 0], p.Fx, nu)
+        errs[scheme] = A.err_norm(fl["ux"][:, 0], th)
+    assert errs[1] < 0.5 * errs[0], errs
+
+
+# ------------------------------------------------------ coexistence -------
+
+
+def test_flat_interface_coexistence_matches_mechanical_stability():
+    """Bulk densities of a converged flat interface follow the mechanical stability
+    condition with the scheme's epsilon (Sec. 1, Eq. (1)), not the Maxwell construction.
+    The periodic slab is read after 80k steps: its centred position is unstable to a
+    slow translation that round-off starts after about 1.4e5 steps."""
+    T, rg, rl = cs_case()
+    ny = 64
+    p = cs_params(nx=1, ny=ny, periodic_x=True, periodic_y=True, scheme=1)
+    s = O.OracleSim(p)
+    s.init(I.tanh_slab(1, ny, rl, rg, ny / 2))
+    O.steady_state(s, 60000, rounds=2, settle=10000)
+    rho = s.moments()[0][:, 0]
+    g_ms, l_ms, _ = A.mechanical_stability(EPS_TC, 1, p.a, p.b, p.R, p.T, p.K_eos)
+    gas, liq = rho.min(), rho.max()
+    assert abs(gas - g_ms) / g_ms < 0.01
+    assert abs(liq - l_ms) / l_ms < 0.01
+    # and differs from Maxwell's gas density by more than that
+    assert abs(gas - rg) / rg > 0.05
+
+
+def test_static_improved_equals_original_at_node_level():
+    """Sec. 2.2: with u = 0 the improved Q_4, Q_6 vanish; with the original Q_2 as well the
+    two schemes give bit-identical collisions."""
+    f = np.array([0.5, 0.125, 0.25, 0.1875, 0.21875, 0.0625, 0.0625, 0.0625, 0.0625])
+    S = (0.25, -0.125)      # F_int = -G psi S = (0.125, -0.0625) with G = -1, psi = 0.5
+    p0 = cs_params(scheme=0)
+    p1 = cs_params(scheme=1, q2_original=True)
+    o0 = O.collide_node(p0, f, 0.5, S)
+    o1 = O.collide_node(p1, f, 0.5, S)
+    assert np.all(o0["u"] == 0.0)
+    assert o1["Q"][4] == 0.0 and o1["Q"][6] == 0.0
+    assert np.array_equal(o0["fbar"], o1["fbar"])
+    p2 = cs_params(scheme=1)
+    o2 = O.collide_node(p2, f, 0.5, S)
+    assert o2["Q"][2] == -o2["Q"][1] / 2 and o0["Q"][2] == -o0["Q"][1]
+
+
+def test_static_flat_interface_same_for_both_schemes():
+    """Grid-aligned static interface: Q_2 does not enter the aligned relations and Q_4,
+    Q_6 vanish with u, so both schemes converge to the same density (Sec. 2.2)."""
+    T, rg, rl = cs_case()
+    ny = 40
+    rhos = []
+    for scheme in (0, 1):
+        p = cs_params(nx=1, ny=ny, periodic_x=True, periodic_y=False, scheme=scheme)
+        s = O.OracleSim(p)
+        s.init(I.tanh_slab(1, ny, rl, rg, ny / 2))
+        O.steady_state(s, 200000, rounds=6, settle=15000)
+        rhos.append(s.moments()[0][:, 0])
+    assert np.abs(rhos[0] - rhos[1]).max() < 1e-11
