@@ -1,0 +1,333 @@
+"""Throughput of the D2Q9 pseudopotential MRT step on the periodic spinodal workload.
+
+Workload: 8192 x 8192 periodic lattice, Carnahan-Starling EOS (a = 1, b = 4, R = 1,
+T = 0.7 T_c), epsilon = 1.895, improved third-order source, tau = 0.8, initial density
+rho = (rho_l + rho_g)/2 (1 + U(-0.01, 0.01)) with SplitMix64 seed 5, u = 0.  One step is
+one lattice update of every node.  Inputs (two 2.4 GB population buffers in FP32) are
+far larger than the 129 MB L2, so no flush is needed between steps.
+
+Prints one JSON line.  --impl reference times the FP64 CPU oracle instead (bounded
+sample of the same workload on the host cores).
+"""
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+RHO_G, RHO_L = 0.009291723294794338, 0.3581443962580134  # Maxwell densities of the EOS at 0.7 T_c
+T_07 = 0.7 * 0.3773 / 4.0
+BYTES = {"f64": 144, "f32": 72, "f16dev": 36, "bf16dev": 36}
+HBM_FALLBACK = 6800.0
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return HBM_FALLBACK, "fallback"
+
+
+def workload_rho(n, seed=5):
+    from paper_2604_13407_gb300 import inputs as I
+    return I.spinodal(n, n, 0.5 * (RHO_L + RHO_G), 0.01, seed)
+
+
+# ------------------------------------------------------------------ clocks --
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_id):
+        self.device_id = device_id
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", self.device_id, "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            time.sleep(0.25)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        rows = []
+        try:
+            for line in open(self.path):
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        except Exception:
+            pass
+        finally:
+            try:
+                os.unlink(self.path)
+            except Exception:
+                pass
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        smax = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            for k, nm in enumerate(names):
+                if r[5 + k].lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(rows)}
+
+
+# -------------------------------------------------------------- GPU legs --
+
+def make_sim(n, precision, scheme=1, kernel=0, per_node_ref=0):
+    import torch
+    from paper_2604_13407_gb300 import lbm
+    p = lbm.default_params(nx=n, ny=n, periodic_x=1, periodic_y=1, precision=precision, scheme=scheme,
+                           kernel=kernel, per_node_ref=per_node_ref, T=T_07, rho_l=RHO_L, rho_g=RHO_G,
+                           rho_s=RHO_G, rho_ref=0.5 * (RHO_L + RHO_G))
+    return lbm.Simulation(p, stream=torch.cuda.current_stream())
+
+
+def timed_steps(sim, steps, warmup, dist_on):
+    import torch
+    sim.step(warmup)
+    torch.cuda.synchronize()
+    if dist_on:
+        torch.distributed.barrier()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    sim.step(steps)
+    e1.record()
+    torch.cuda.synchronize()
+    if dist_on:
+        torch.distributed.barrier()
+    t = e0.elapsed_time(e1) / 1e3
+    if dist_on:
+        tt = torch.tensor([t], device="cuda", dtype=torch.float64)
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        t = float(tt.item())
+    return t
+
+
+def per_launch_time(sim, launches=20):
+    """Average duration of one step (the dominant kernel when the fused path runs),
+    CUDA events on the stream the library launches on (torch's current stream)."""
+    import torch
+    ts = []
+    for _ in range(launches):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        sim.step(1)
+        e1.record()
+        e1.synchronize()
+        ts.append(e0.elapsed_time(e1) / 1e3)
+    return sum(ts) / len(ts)
+
+
+def e2e_glups(n, precision, steps, rho_host):
+    """Same metric through the public API with host buffers: H2D of the initial density
+    (pinned), `steps` steps, D2H of rho, ux, uy; all inside the timed region."""
+    import torch
+    from paper_2604_13407_gb300 import lbm
+    sim = make_sim(n, precision)
+    pinned = torch.from_numpy(rho_host.reshape(-1)).pin_memory()
+    out = [torch.empty(n * n, dtype=torch.float64).pin_memory() for _ in range(3)]
+    h = pinned.numpy()
+    sim.init_fields(h)
+    sim.step(2)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    sim.init_fields(h)
+    sim.step(steps)
+    r, u, v = sim.moments()
+    torch.cuda.synchronize()
+    t = time.perf_counter() - t0
+    sim.close()
+    del out
+    return n * n * steps / t / 1e9, 8 * n * n / steps, 3 * 8 * n * n / steps
+
+
+# ------------------------------------------------------------ CPU legs ----
+
+def oracle_glups(n, seconds_target=10.0, max_steps=50):
+    """The FP64 oracle on an n x n sample of the workload; returns (GLUPS, steps, threads)."""
+    from oracle import oracle as O
+    p = O.Params(nx=n, ny=n, periodic_x=True, periodic_y=True, scheme=1, T=T_07, rho_l=RHO_L,
+                 rho_g=RHO_G, rho_s=RHO_G)
+    s = O.OracleSim(p)
+    s.init(workload_rho(n))
+    t0 = time.perf_counter()
+    s.step(1)
+    t1 = time.perf_counter() - t0
+    steps = int(max(1, min(max_steps, seconds_target / max(t1, 1e-6))))
+    t0 = time.perf_counter()
+    s.step(steps)
+    t = time.perf_counter() - t0
+    threads = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    return n * n * steps / t / 1e9, steps, threads
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    n = args.ref_sample
+    from oracle import oracle as O
+    p = O.Params(nx=n, ny=n, periodic_x=True, periodic_y=True, scheme=1, T=T_07, rho_l=RHO_L,
+                 rho_g=RHO_G, rho_s=RHO_G)
+    s = O.OracleSim(p)
+    s.init(workload_rho(n))
+    s.step(args.warmup)
+    t0 = time.perf_counter()
+    s.step(args.steps)
+    t = time.perf_counter() - t0
+    v = n * n * args.steps / t / 1e9
+    threads = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    line = {"impl": "reference", "metric": "GLUPS", "value": v, "unit": "GLUPS", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": "spinodal %dx%d periodic sample of the 8192x8192 workload "
+                                   "(CS 0.7Tc, eps 1.895, improved scheme)" % (n, n), "nx": n, "ny": n},
+            "cpu_baseline": {"value": v, "unit": "GLUPS", "cores": threads, "kind": "oracle",
+                             "sample": "%dx%d lattice, %d steps" % (n, n, args.steps)},
+            "e2e": {"value": v, "unit": "GLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n", type=int, default=8192)
+    ap.add_argument("--precision", default="f32", choices=["f64", "f32", "f16dev", "bf16dev"])
+    ap.add_argument("--variants", type=int, default=1, help="also time the other precisions / scheme")
+    ap.add_argument("--cpu-baseline", type=int, default=1)
+    ap.add_argument("--ref-sample", type=int, default=512)
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    from paper_2604_13407_gb300 import lbm
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist_on = world > 1
+    if dist_on:
+        torch.cuda.set_device(local)
+        torch.distributed.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    prec_id = {"f64": lbm.F64, "f32": lbm.F32, "f16dev": lbm.F16DEV, "bf16dev": lbm.BF16DEV}
+    n = args.n
+    rho = workload_rho(n, seed=5 + rank)
+    hbm, peak_kind = peaks()
+    dev_uuid = str(torch.cuda.get_device_properties(torch.cuda.current_device()).uuid)
+    if not dev_uuid.startswith("GPU-"):
+        dev_uuid = "GPU-" + dev_uuid
+
+    sim = make_sim(n, prec_id[args.precision])
+    sim.init_fields(rho)
+    kernels_per_step = 1 if sim.kernel_in_use == lbm.KERNEL_FUSED else 2
+    with ClockSampler(dev_uuid) as clk:
+        t = timed_steps(sim, args.steps, args.warmup, dist_on)
+    clocks = clk.summary()
+    t_launch = per_launch_time(sim)
+    d = sim.diagnostics()
+    sim.close()
+    updates = float(n) * n * args.steps * world
+    value = updates / t / 1e9
+    bpu = BYTES[args.precision]
+    achieved = bpu * n * n / t_launch / 1e9
+
+    variants = {}
+    if args.variants and rank == 0 and not dist_on:
+        for name, prec, scheme, extra in (("f32_original", "f32", 0, {}), ("f16dev", "f16dev", 1, {}),
+                                          ("bf16dev", "bf16dev", 1, {}), ("f16dev_node_ref", "f16dev", 1, {"per_node_ref": 1}),
+                                          ("f64", "f64", 1, {})):
+            if prec == args.precision and scheme == 1 and not extra:
+                continue
+            s2 = make_sim(n, prec_id[prec], scheme=scheme, **extra)
+            s2.init_fields(rho)
+            k = max(20, args.steps // (4 if prec == "f64" else 1))
+            t2 = timed_steps(s2, k, args.warmup, False)
+            tl = per_launch_time(s2, 5)
+            b = BYTES[prec] + (8 if extra.get("per_node_ref") else 0)
+            variants[name] = {"GLUPS": n * n * k / t2 / 1e9, "bytes_per_update": b,
+                              "achieved_GBs": b * n * n / tl / 1e9, "frac": b * n * n / tl / 1e9 / hbm,
+                              "kernel": "fused" if s2.kernel_in_use == lbm.KERNEL_FUSED else "two_pass"}
+            s2.close()
+
+    e2e = None
+    if rank == 0:
+        ev, hb, db = e2e_glups(n, prec_id[args.precision], args.steps, rho)
+        e2e = {"value": ev, "unit": "GLUPS", "h2d_bytes_per_step": hb, "d2h_bytes_per_step": db}
+    cpu = None
+    if args.cpu_baseline and rank == 0 and not dist_on:
+        g, st, threads = oracle_glups(1024)
+        cpu = {"value": g, "unit": "GLUPS", "cores": threads, "kind": "oracle",
+               "sample": "1024x1024 periodic spinodal, %d steps, FP64" % st}
+    if rank == 0:
+        line = {
+            "metric": "GLUPS", "value": value, "unit": "GLUPS", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32" if args.precision != "f64" else "f64",
+            "data": "synthetic",
+            "config": {"workload": "spinodal %dx%d periodic, Carnahan-Starling 0.7Tc, eps 1.895, improved "
+                                   "scheme, tau 0.8, %s population storage" % (n, n, args.precision),
+                       "nx": n, "ny": n, "storage": args.precision,
+                       "l2": "inputs larger than L2 (population buffers %.1f GB each)" % (bpu / 2 * n * n / 1e9),
+                       "parallelism": "replicas" if world > 1 else "single"},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                         "frac": achieved / hbm, "traffic": None, "peak_kind": peak_kind,
+                         "bytes_per_update": bpu,
+                         "kernel": "fused" if kernels_per_step == 1 else "two_pass (step)"},
+            "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": args.steps * kernels_per_step,
+            "clocks": clocks, "variants": variants,
+            "mass": d[0],
+        }
+        print(json.dumps(line))
+    if dist_on:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,22 @@
+// Kernel instantiations for __half population storage.
+#include "k_twopass.cuh"
+
+namespace lbm {
+
+Launchers launchers_f16()
+{
+    Launchers L{};
+    L.psi_pass = &TwoPass<__half>::psi_pass;
+    L.collide_pass = &TwoPass<__half>::collide_pass;
+    L.fused_pass = nullptr;
+    L.init = &TwoPass<__half>::init;
+    L.moments = &TwoPass<__half>::moments;
+    L.diag = &TwoPass<__half>::diag;
+    L.get_state = &TwoPass<__half>::get_state;
+    L.set_state = &TwoPass<__half>::set_state;
+    L.fused_tile_x = 0;
+    L.fused_align = 0;
+    return L;
+}
+
+}  // namespace lbm

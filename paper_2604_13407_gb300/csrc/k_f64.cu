@@ -1,0 +1,22 @@
+// Kernel instantiations for double population storage.
+#include "k_twopass.cuh"
+
+namespace lbm {
+
+Launchers launchers_f64()
+{
+    Launchers L{};
+    L.psi_pass = &TwoPass<double>::psi_pass;
+    L.collide_pass = &TwoPass<double>::collide_pass;
+    L.fused_pass = nullptr;
+    L.init = &TwoPass<double>::init;
+    L.moments = &TwoPass<double>::moments;
+    L.diag = &TwoPass<double>::diag;
+    L.get_state = &TwoPass<double>::get_state;
+    L.set_state = &TwoPass<double>::set_state;
+    L.fused_tile_x = 0;
+    L.fused_align = 0;
+    return L;
+}
+
+}  // namespace lbm

@@ -1,0 +1,37 @@
+// Adjoint driver interface (checkpointed backward pass of the step).
+#pragma once
+
+#include <string>
+
+#include "../../include/lbm.h"
+#include "lbm_internal.h"
+
+namespace lbm {
+
+struct AdjointState;  // device buffers owned by the adjoint driver
+
+// What the adjoint driver may see of a context.
+struct ContextView {
+    const lbm_params *p;
+    KParams *kp;
+    cudaStream_t stream;
+    void **pops;
+    float **refp;
+    int *cur;
+    int64_t *steps;
+    size_t elem;
+    int64_t plane;
+    AdjointState **adj;
+    lbm_status (*run_steps)(lbm_ctx *, int64_t);
+    void (*bind)(lbm_ctx *, int);
+    cudaError_t (*psi_pass)(const KParams &, cudaStream_t);
+    cudaError_t (*collide_pass)(const KParams &, cudaStream_t);
+    lbm_ctx *ctx;
+};
+
+ContextView view_of(lbm_ctx *c);
+void adjoint_free(AdjointState *a);
+lbm_status adjoint_run(lbm_ctx *c, int64_t nsteps, int32_t checkpoint_every, int32_t objective, double *J,
+                       double grad[4], double *lambda0, std::string &msg);
+
+}  // namespace lbm

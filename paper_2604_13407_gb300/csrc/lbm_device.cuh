@@ -1,0 +1,340 @@
+// Device building blocks of the D2Q9 pseudopotential MRT step: lattice constants,
+// storage codecs, EOS pseudopotential, pull streaming with wall links, collision.
+// Every kernel variant calls these same functions in the same order, so the two-pass
+// and the fused kernels produce bit-identical populations.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
+#include "lbm_internal.h"
+
+namespace lbm {
+
+// ---------------------------------------------------------------- lattice --
+// D2Q9: e_0 = (0,0); e_1..e_4 = (1,0),(0,1),(-1,0),(0,-1); e_5..e_8 = (1,1),(-1,1),
+// (-1,-1),(1,-1) -- the numbering the sums of Eqs. (ali.2) and (obl.3) use.
+__host__ __device__ constexpr int ex_(int i) { return (i == 1 || i == 5 || i == 8) ? 1 : ((i == 3 || i == 6 || i == 7) ? -1 : 0); }
+__host__ __device__ constexpr int ey_(int i) { return (i == 2 || i == 5 || i == 6) ? 1 : ((i == 4 || i == 7 || i == 8) ? -1 : 0); }
+__host__ __device__ constexpr int opp_(int i) { return i == 0 ? 0 : (i <= 4 ? ((i + 1) % 4) + 1 : ((i - 3) % 4) + 5); }
+template <class R>
+__host__ __device__ constexpr R w_(int i) { return i == 0 ? R(4.0 / 9.0) : (i <= 4 ? R(1.0 / 9.0) : R(1.0 / 36.0)); }
+// Eq. (fint) nearest-neighbour weights: w(1) = 1/3, w(2) = 1/12
+template <class R>
+__host__ __device__ constexpr R omega_(int i) { return i == 0 ? R(0) : (i <= 4 ? R(1.0 / 3.0) : R(1.0 / 12.0)); }
+
+// ------------------------------------------------------------ codecs -------
+// Stored value <-> population.  FP16/BF16 keep (f_i - w_i rho_ref) 2^k, rounded to
+// nearest even; decode multiplies back by 2^-k (exact) and adds w_i rho_ref.
+template <class S> struct Codec;
+template <> struct Codec<double> {
+    typedef double R;
+    static __device__ __forceinline__ R dec(double v, R, R) { return v; }
+    static __device__ __forceinline__ double enc(R f, R, R) { return f; }
+};
+template <> struct Codec<float> {
+    typedef float R;
+    static __device__ __forceinline__ R dec(float v, R, R) { return v; }
+    static __device__ __forceinline__ float enc(R f, R, R) { return f; }
+};
+template <> struct Codec<__half> {
+    typedef float R;
+    static __device__ __forceinline__ R dec(__half v, R wref, R inv_scale) { return __half2float(v) * inv_scale + wref; }
+    static __device__ __forceinline__ __half enc(R f, R wref, R scale) { return __float2half_rn((f - wref) * scale); }
+};
+template <> struct Codec<__nv_bfloat16> {
+    typedef float R;
+    static __device__ __forceinline__ R dec(__nv_bfloat16 v, R wref, R inv_scale) { return __bfloat162float(v) * inv_scale + wref; }
+    static __device__ __forceinline__ __nv_bfloat16 enc(R f, R wref, R scale) { return __float2bfloat16_rn((f - wref) * scale); }
+};
+template <class S> struct IsDev { static constexpr bool value = false; };
+template <> struct IsDev<__half> { static constexpr bool value = true; };
+template <> struct IsDev<__nv_bfloat16> { static constexpr bool value = true; };
+
+// ------------------------------------------------------------- EOS ---------
+// Sec. 2: psi = sqrt(2 (p_EOS - rho c_s^2)/G); van der Waals (Sec. 3) or Carnahan-Starling.
+template <class R>
+__device__ __forceinline__ R p_eos(const KParams &kp, R rho)
+{
+    const R a = R(kp.eos_a), b = R(kp.eos_b), RT = R(kp.eos_RT), K = R(kp.eos_K);
+    if (kp.eos == 0) return K * (rho * RT / (R(1) - b * rho) - a * rho * rho);
+    const R eta = b * rho * R(0.25);
+    const R om = R(1) - eta;
+    const R num = R(1) + eta + eta * eta - eta * eta * eta;
+    return K * (rho * RT * num / (om * om * om) - a * rho * rho);
+}
+
+template <class R>
+__device__ __forceinline__ R psi_of(const KParams &kp, R rho)
+{
+    return sqrt(R(kp.two_over_G) * (p_eos<R>(kp, rho) - rho / R(3)));
+}
+
+// ------------------------------------------------------------ geometry -----
+// Wrap (x, y) along periodic directions; false when the point lies beyond a
+// non-periodic edge (a wall).  Only offsets of one node are ever wrapped.
+__device__ __forceinline__ bool wrap_xy(const KParams &kp, int &x, int &y)
+{
+    if (x < 0 || x >= kp.nx) {
+        if (!kp.periodic_x) return false;
+        x = (x < 0) ? x + kp.nx : x - kp.nx;
+    }
+    if (y < 0 || y >= kp.ny) {
+        if (!kp.periodic_y) return false;
+        y = (y < 0) ? y + kp.ny : y - kp.ny;
+    }
+    return true;
+}
+
+__device__ __forceinline__ bool is_wall_at(const KParams &kp, int x, int y)
+{
+    if (!wrap_xy(kp, x, y)) return true;
+    return kp.solid != nullptr && kp.solid[(int64_t)y * kp.nx + x] != 0;
+}
+
+// ------------------------------------------------------- global access ------
+// Population i of node (x, y) of the source state, decoded.
+template <class S>
+__device__ __forceinline__ typename Codec<S>::R load_pop(const KParams &kp, int i, int x, int y)
+{
+    typedef typename Codec<S>::R R;
+    const S *A = static_cast<const S *>(kp.src);
+    const int64_t k = (int64_t)y * kp.pitch + x;
+    R wref = R(0);
+    if (IsDev<S>::value) wref = w_<R>(i) * (kp.per_node_ref ? R(kp.ref_src[k]) : R(kp.rho_ref));
+    return Codec<S>::dec(A[i * kp.plane + k], wref, R(kp.inv_scale));
+}
+
+// Link closed by a wall (x - e_i is a wall): the population that left (x, y) toward it
+// comes back.  `at(k, xx, yy)` reads population k of node (xx, yy) (xx, yy in domain).
+// half-way (q = 1/2): f_i = fbar_o(x) + mw
+// q <  1/2: f_i = 2q fbar_o(x) + (1 - 2q) fbar_o(x + e_i) + mw          (Bouzidi et al.)
+// q >  1/2: f_i = fbar_o(x)/(2q) + (2q - 1)/(2q) fbar_i(x) + mw/(2q)
+// mw = 2 w_o rho_w (e_i . u_w)/c_s^2 with rho_w = sum_k fbar_k(x) (Lallemand & Luo).
+// mom (may be null) accumulates the momentum handed to the wall, -e_i (fbar_o(x) + f_i).
+template <class R, int i, class At>
+__device__ __forceinline__ R bounce(const KParams &kp, int x, int y, const At &at, R *mom)
+{
+    constexpr int o = opp_(i);
+    const R fo = at(o, x, y);
+    R mw = R(0);
+    if (kp.wall_u != nullptr) {
+        int wx = x - ex_(i), wy = y - ey_(i);
+        if (wrap_xy(kp, wx, wy)) {
+            const int64_t wk = (int64_t)wy * kp.nx + wx;
+            const R uwx = R(kp.wall_u[wk]);
+            const R uwy = R(kp.wall_u[(int64_t)kp.nx * kp.ny + wk]);
+            R rho_w = R(0);
+#pragma unroll
+            for (int k = 0; k < 9; ++k) rho_w += at(k, x, y);
+            mw = R(2) * w_<R>(o) * rho_w * (R(ex_(i)) * uwx + R(ey_(i)) * uwy) * R(3);
+        }
+    }
+    R q = R(0.5);
+    if (kp.q != nullptr) q = R(kp.q[(int64_t)(o - 1) * kp.nx * kp.ny + (int64_t)y * kp.nx + x]);
+    int xb = x + ex_(i), yb = y + ey_(i);
+    if (q < R(0.5) && is_wall_at(kp, xb, yb)) q = R(0.5);
+    R f;
+    if (q < R(0.5)) {
+        wrap_xy(kp, xb, yb);
+        f = R(2) * q * fo + (R(1) - R(2) * q) * at(o, xb, yb) + mw;
+    } else if (q == R(0.5)) {
+        f = fo + mw;
+    } else {
+        f = fo / (R(2) * q) + (R(2) * q - R(1)) / (R(2) * q) * at(i, x, y) + mw / (R(2) * q);
+    }
+    if (mom != nullptr) {
+        mom[0] += -R(ex_(i)) * (fo + f);
+        mom[1] += -R(ey_(i)) * (fo + f);
+    }
+    return f;
+}
+
+// Pull streaming, Eq. (lbe.str): f_i(x) = fbar_i(x - e_i), wall links bounced back.
+template <class R, int i, class At>
+__device__ __forceinline__ R pull_one(const KParams &kp, int x, int y, const At &at, R *mom)
+{
+    if (i == 0) return at(0, x, y);
+    int xs = x - ex_(i), ys = y - ey_(i);
+    const bool inside = wrap_xy(kp, xs, ys);
+    if (inside && (kp.solid == nullptr || kp.solid[(int64_t)ys * kp.nx + xs] == 0)) return at(i, xs, ys);
+    return bounce<R, i>(kp, x, y, at, mom);
+}
+
+template <class R, class At>
+__device__ __forceinline__ void pull_node(const KParams &kp, int x, int y, const At &at, R (&f)[9], R *mom)
+{
+    f[0] = pull_one<R, 0>(kp, x, y, at, mom);
+    f[1] = pull_one<R, 1>(kp, x, y, at, mom);
+    f[2] = pull_one<R, 2>(kp, x, y, at, mom);
+    f[3] = pull_one<R, 3>(kp, x, y, at, mom);
+    f[4] = pull_one<R, 4>(kp, x, y, at, mom);
+    f[5] = pull_one<R, 5>(kp, x, y, at, mom);
+    f[6] = pull_one<R, 6>(kp, x, y, at, mom);
+    f[7] = pull_one<R, 7>(kp, x, y, at, mom);
+    f[8] = pull_one<R, 8>(kp, x, y, at, mom);
+}
+
+template <class R>
+__device__ __forceinline__ R density(const R (&f)[9])
+{
+    return (((f[0] + f[1]) + (f[2] + f[3])) + ((f[4] + f[5]) + (f[6] + f[7]))) + f[8];
+}
+
+// ------------------------------------------------------------ forces -------
+template <class R>
+__device__ __forceinline__ void external_force(const KParams &kp, int64_t node, R rho, R &Fex, R &Fey)
+{
+    if (kp.force_mode == 0) {
+        Fex = R(kp.Fx);
+        Fey = R(kp.Fy);
+    } else if (kp.force_mode == 1) {  // Sec. 3.3: (rho - rho_g) g
+        Fex = (rho - R(kp.rho_g)) * R(kp.Fx);
+        Fey = (rho - R(kp.rho_g)) * R(kp.Fy);
+    } else {
+        Fex = kp.fext ? R(kp.fext[node]) : R(0);
+        Fey = kp.fext ? R(kp.fext[(int64_t)kp.nx * kp.ny + node]) : R(0);
+    }
+}
+
+// S = sum_{i=1..8} w(|e_i|^2) psi(x + e_i) e_i, so F_int = -G psi(x) S (Eq. fint).
+// `ps(i)` returns psi of the neighbour along e_i.
+template <class R, class Ps>
+__device__ __forceinline__ void stencil_S(const Ps &ps, R &Sx, R &Sy)
+{
+    const R p1 = ps(1), p2 = ps(2), p3 = ps(3), p4 = ps(4);
+    const R p5 = ps(5), p6 = ps(6), p7 = ps(7), p8 = ps(8);
+    const R a = R(1.0 / 3.0), d = R(1.0 / 12.0);
+    Sx = a * (p1 - p3) + d * ((p5 - p7) + (p8 - p6));
+    Sy = a * (p2 - p4) + d * ((p5 - p7) + (p6 - p8));
+}
+
+// --------------------------------------------------------- collision -------
+// Stages 5-8 of a node: u = (j + F/2)/rho (Eq. rho.rhou); m = M f; m_eq, F_m (Sec. 2);
+// Q_m original or improved (Eqs. qm.improved, qm46.improved); rates s_0 = s_j = 1,
+// s_e = s_eps = s_p = 1/tau, (1/s_q - 1/2)(1/s_p - 1/2) = Lambda (Sec. 3);
+// m_bar = m + F_m - S (m - m_eq + F_m/2) + S Q_m (Eq. lbe.col); f_bar = M^-1 m_bar.
+template <class R>
+__device__ __forceinline__ void collide(const KParams &kp, const R (&f)[9], R rho, R psi, R Sx, R Sy,
+                                        R Fex, R Fey, R (&fb)[9], R &ux, R &uy)
+{
+    const R G = R(kp.G);
+    const R jx = ((f[1] - f[3]) + (f[5] - f[6])) + (f[8] - f[7]);
+    const R jy = ((f[2] - f[4]) + (f[5] + f[6])) - (f[7] + f[8]);
+    const R Fix = -G * psi * Sx, Fiy = -G * psi * Sy;
+    const R Fx = Fix + Fex, Fy = Fiy + Fey;
+    const R inv = R(1) / rho;
+    ux = (jx + R(0.5) * Fx) * inv;
+    uy = (jy + R(0.5) * Fy) * inv;
+
+    // non-conserved moments of M f
+    const R s14 = (f[1] + f[2]) + (f[3] + f[4]);
+    const R s58 = (f[5] + f[6]) + (f[7] + f[8]);
+    const R m1 = R(-4) * f[0] - s14 + R(2) * s58;
+    const R m2 = R(4) * f[0] - R(2) * s14 + s58;
+    const R m4 = R(-2) * (f[1] - f[3]) + ((f[5] - f[6]) + (f[8] - f[7]));
+    const R m6 = R(-2) * (f[2] - f[4]) + ((f[5] + f[6]) - (f[7] + f[8]));
+    const R m7 = (f[1] + f[3]) - (f[2] + f[4]);
+    const R m8 = (f[5] + f[7]) - (f[6] + f[8]);
+
+    // equilibrium and forcing moments
+    const R u2 = ux * ux + uy * uy;
+    const R meq1 = rho * (R(-2) + R(3) * u2);
+    const R meq2 = rho * (R(1) - R(3) * u2);
+    const R meq4 = -rho * ux, meq6 = -rho * uy;
+    const R meq7 = rho * (ux * ux - uy * uy), meq8 = rho * ux * uy;
+    const R Fu = Fx * ux + Fy * uy;
+    const R Fm1 = R(6) * Fu, Fm2 = R(-6) * Fu, Fm4 = -Fx, Fm6 = -Fy;
+    const R Fm7 = R(2) * (Fx * ux - Fy * uy), Fm8 = Fx * uy + Fy * ux;
+
+    // third-order source with |F_int|^2/(G psi^2) = G |S|^2
+    const R Sx2 = Sx * Sx, Sy2 = Sy * Sy;
+    const R Q1 = R(kp.kq1) * (Sx2 + Sy2);
+    const R Q2 = R(kp.q2fac) * Q1;
+    const R Q7 = R(kp.kq7) * (Sx2 - Sy2);
+    const R Q8 = R(kp.kq7) * Sx * Sy;
+    R Q4 = R(0), Q6 = R(0);
+    if (kp.improved) {
+        Q4 = (R(kp.c1G) * Sx2 - R(kp.c2G) * Sy2) * ux;
+        Q6 = (R(kp.c1G) * Sy2 - R(kp.c2G) * Sx2) * uy;
+    }
+
+    R sp = R(kp.sp), sq = R(kp.sq);
+    if (kp.var_tau) {
+        R wgt = (rho - R(kp.rho_g)) / (R(kp.rho_l) - R(kp.rho_g));
+        wgt = wgt < R(0) ? R(0) : (wgt > R(1) ? R(1) : wgt);
+        const R nu = R(kp.nu_g) + wgt * (R(kp.nu_l) - R(kp.nu_g));
+        const R tau = R(3) * nu + R(0.5);
+        sp = R(1) / tau;
+        sq = R(1) / (R(0.5) + R(kp.Lambda) / (tau - R(0.5)));
+    }
+    const R hsp = R(1) - R(0.5) * sp, hsq = R(1) - R(0.5) * sq;
+    // m_bar = (1 - s) m + s m_eq + (1 - s/2) F_m + s Q   (same as Eq. lbe.col)
+    const R b1 = m1 - sp * (m1 - meq1) + hsp * Fm1 + sp * Q1;
+    const R b2 = m2 - sp * (m2 - meq2) + hsp * Fm2 + sp * Q2;
+    const R b4 = m4 - sq * (m4 - meq4) + hsq * Fm4 + sq * Q4;
+    const R b6 = m6 - sq * (m6 - meq6) + hsq * Fm6 + sq * Q6;
+    const R b7 = m7 - sp * (m7 - meq7) + hsp * Fm7 + sp * Q7;
+    const R b8 = m8 - sp * (m8 - meq8) + hsp * Fm8 + sp * Q8;
+    const R b3 = jx + Fx, b5 = jy + Fy;  // s_j = 1: m_bar_j = rho u + F/2 = j + F
+
+    // f_bar = M^T diag(1/9, 1/36, 1/36, 1/6, 1/12, 1/6, 1/12, 1/4, 1/4) m_bar
+    const R A0 = rho * R(1.0 / 9.0), B = b1 * R(1.0 / 36.0), C = b2 * R(1.0 / 36.0);
+    const R D = b3 * R(1.0 / 6.0), E = b4 * R(1.0 / 12.0), Gy = b5 * R(1.0 / 6.0), H = b6 * R(1.0 / 12.0);
+    const R P = b7 * R(0.25), Qp = b8 * R(0.25);
+    const R ax = A0 - B - R(2) * C;   // axis directions
+    const R dg = A0 + R(2) * B + C;   // diagonal directions
+    fb[0] = A0 - R(4) * B + R(4) * C;
+    fb[1] = ax + (D - R(2) * E) + P;
+    fb[2] = ax + (Gy - R(2) * H) - P;
+    fb[3] = ax - (D - R(2) * E) + P;
+    fb[4] = ax - (Gy - R(2) * H) - P;
+    fb[5] = dg + (D + E) + (Gy + H) + Qp;
+    fb[6] = dg - (D + E) + (Gy + H) - Qp;
+    fb[7] = dg - (D + E) - (Gy + H) + Qp;
+    fb[8] = dg + (D + E) - (Gy + H) - Qp;
+}
+
+// f_bar = M^-1 m_eq(rho, u): the equilibrium used by lbm_init_fields
+template <class R>
+__device__ __forceinline__ void equilibrium(R rho, R ux, R uy, R (&fb)[9])
+{
+    const R u2 = ux * ux + uy * uy;
+    const R b1 = rho * (R(-2) + R(3) * u2), b2 = rho * (R(1) - R(3) * u2);
+    const R b3 = rho * ux, b4 = -rho * ux, b5 = rho * uy, b6 = -rho * uy;
+    const R b7 = rho * (ux * ux - uy * uy), b8 = rho * ux * uy;
+    const R A0 = rho * R(1.0 / 9.0), B = b1 * R(1.0 / 36.0), C = b2 * R(1.0 / 36.0);
+    const R D = b3 * R(1.0 / 6.0), E = b4 * R(1.0 / 12.0), Gy = b5 * R(1.0 / 6.0), H = b6 * R(1.0 / 12.0);
+    const R P = b7 * R(0.25), Qp = b8 * R(0.25);
+    const R ax = A0 - B - R(2) * C;
+    const R dg = A0 + R(2) * B + C;
+    fb[0] = A0 - R(4) * B + R(4) * C;
+    fb[1] = ax + (D - R(2) * E) + P;
+    fb[2] = ax + (Gy - R(2) * H) - P;
+    fb[3] = ax - (D - R(2) * E) + P;
+    fb[4] = ax - (Gy - R(2) * H) - P;
+    fb[5] = dg + (D + E) + (Gy + H) + Qp;
+    fb[6] = dg - (D + E) + (Gy + H) - Qp;
+    fb[7] = dg - (D + E) - (Gy + H) + Qp;
+    fb[8] = dg + (D + E) - (Gy + H) - Qp;
+}
+
+// Encode and store the nine post-collision populations of node (x, y) into dst.
+template <class S>
+__device__ __forceinline__ void store_node(const KParams &kp, int x, int y, const typename Codec<S>::R (&fb)[9],
+                                           typename Codec<S>::R rho)
+{
+    typedef typename Codec<S>::R R;
+    S *Bp = static_cast<S *>(kp.dst);
+    const int64_t k = (int64_t)y * kp.pitch + x;
+    R ref = R(kp.rho_ref);
+    if (IsDev<S>::value && kp.per_node_ref) {
+        ref = rho;
+        kp.ref_dst[k] = float(rho);
+    }
+    const R scale = R(kp.scale);
+#pragma unroll
+    for (int i = 0; i < 9; ++i) Bp[i * kp.plane + k] = Codec<S>::enc(fb[i], w_<R>(i) * ref, scale);
+}
+
+}  // namespace lbm

@@ -1,0 +1,78 @@
+// Internal types shared by the host API and the kernel translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace lbm {
+
+// Everything a kernel needs, passed by value.  Physical constants are kept in double
+// and converted to the arithmetic type of each kernel at its start.
+struct KParams {
+    int nx, ny;
+    int64_t pitch;  // elements per row of a population plane (and of the rho_ref plane)
+    int64_t plane;  // elements per population plane = pitch * ny
+    int periodic_x, periodic_y;
+    int improved;    // 1: improved Q4, Q6 (Eq. qm46.improved)
+    int eos;         // 0 van der Waals, 1 Carnahan-Starling
+    int force_mode;  // 0 constant, 1 (rho - rho_g) g, 2 field
+    int var_tau;     // 1: tau(rho) from the linear nu(rho) interpolation
+    int per_node_ref;
+    // EOS: p = K (rho RT g(rho) - a rho^2); psi = sqrt(two_over_G (p - rho/3))
+    double eos_a, eos_b, eos_RT, eos_K, two_over_G;
+    double G;
+    // source term with G folded in (|F_int|^2/(G psi^2) = G |S|^2, S = F_int/(-G psi)):
+    // Q1 = kq1 |S|^2, Q2 = q2fac Q1, Q7 = kq7 (Sx^2 - Sy^2), Q8 = kq7 Sx Sy,
+    // Q4 = (c1G Sx^2 - c2G Sy^2) ux, Q6 = (c1G Sy^2 - c2G Sx^2) uy
+    double kq1, kq7, c1G, c2G, q2fac;
+    // relaxation: constant rates, or nu(rho) interpolation data
+    double sp, sq;
+    double nu_l, nu_g, rho_l, rho_g, Lambda;
+    double Fx, Fy;
+    double psi_s;  // psi(rho_s) of walls
+    double rho_s;
+    // FP16/BF16 storage codec
+    double rho_ref, scale, inv_scale;
+    // buffers
+    const void *src;       // populations read (post-collision state of the last step)
+    void *dst;             // populations written
+    const float *ref_src;  // per-node reference density planes (FP16/BF16 with per_node_ref)
+    float *ref_dst;
+    void *psi;             // psi field [ny*nx] in the kernel's arithmetic type
+    const uint8_t *solid;  // [ny*nx] or null
+    const double *wall_u;  // [2][ny*nx] or null
+    const double *q;       // [8][ny*nx] or null
+    const double *fext;    // [2][ny*nx] or null
+    int *err;              // device error word (0 = fine)
+};
+
+// Storage precisions (match lbm_precision)
+enum Prec { P_F64 = 0, P_F32 = 1, P_F16 = 2, P_BF16 = 3 };
+
+// Device error word bits
+enum DevErr { DERR_TIMEOUT = 1, DERR_BOUNDS = 2 };
+
+// Launchers, defined in the per-precision translation units (k_f64.cu, k_f32.cu,
+// k_f16.cu).  All run on `st` and return the launch status.
+struct Launchers {
+    cudaError_t (*psi_pass)(const KParams &, cudaStream_t);
+    cudaError_t (*collide_pass)(const KParams &, cudaStream_t);
+    cudaError_t (*fused_pass)(const KParams &, cudaStream_t);  // may be null
+    cudaError_t (*init)(const KParams &, const double *rho, const double *ux, const double *uy,
+                        cudaStream_t);
+    cudaError_t (*moments)(const KParams &, double *rho, double *ux, double *uy, cudaStream_t);
+    cudaError_t (*diag)(const KParams &, double *acc, unsigned long long *umax, int *nan_count,
+                        cudaStream_t);
+    cudaError_t (*get_state)(const KParams &, double *out, cudaStream_t);
+    cudaError_t (*set_state)(const KParams &, const double *in, cudaStream_t);
+    // fused kernel launch constraints
+    int fused_tile_x;     // strip width in nodes
+    int fused_align;      // nx must be a multiple of this
+};
+
+Launchers launchers_f64();
+Launchers launchers_f32();
+Launchers launchers_f16();
+Launchers launchers_bf16();
+
+}  // namespace lbm
