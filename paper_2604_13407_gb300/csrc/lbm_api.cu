@@ -159,6 +159,10 @@ static void fill_constants(lbm_ctx *c)
     k.eos_RT = p.R * p.T;
     k.eos_K = p.K_eos;
     k.two_over_G = 2.0 / p.G;
+    k.eos_R = p.R;
+    k.eos_T = p.T;
+    k.k1 = p.k1;
+    k.k2 = p.k2;
     k.G = p.G;
     const double eps = -8.0 * (p.k1 + p.k2);
     k.kq1 = 3.0 * (p.k1 + 2.0 * p.k2) * p.G;

@@ -7,6 +7,8 @@
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
+#include <type_traits>
+
 #include "lbm_internal.h"
 
 namespace lbm {
@@ -22,6 +24,15 @@ __host__ __device__ constexpr R w_(int i) { return i == 0 ? R(4.0 / 9.0) : (i <=
 // Eq. (fint) nearest-neighbour weights: w(1) = 1/3, w(2) = 1/12
 template <class R>
 __host__ __device__ constexpr R omega_(int i) { return i == 0 ? R(0) : (i <= 4 ? R(1.0 / 3.0) : R(1.0 / 12.0)); }
+
+}  // namespace lbm
+
+#include "lbm_f64.cuh"
+
+namespace lbm {
+
+template <class R>
+constexpr bool is_f64() { return std::is_same<R, double>::value; }
 
 // ------------------------------------------------------------ codecs -------
 // Stored value <-> population.  FP16/BF16 keep (f_i - w_i rho_ref) 2^k, rounded to
@@ -67,7 +78,8 @@ __device__ __forceinline__ R p_eos(const KParams &kp, R rho)
 template <class R>
 __device__ __forceinline__ R psi_of(const KParams &kp, R rho)
 {
-    return sqrt(R(kp.two_over_G) * (p_eos<R>(kp, rho) - rho / R(3)));
+    if constexpr (is_f64<R>()) return f64::psi_of(kp, rho);
+    else return sqrt(R(kp.two_over_G) * (p_eos<R>(kp, rho) - rho / R(3)));
 }
 
 // ------------------------------------------------------------ geometry -----
@@ -178,7 +190,8 @@ __device__ __forceinline__ void pull_node(const KParams &kp, int x, int y, const
 template <class R>
 __device__ __forceinline__ R density(const R (&f)[9])
 {
-    return (((f[0] + f[1]) + (f[2] + f[3])) + ((f[4] + f[5]) + (f[6] + f[7]))) + f[8];
+    if constexpr (is_f64<R>()) return f64::density(f);
+    else return (((f[0] + f[1]) + (f[2] + f[3])) + ((f[4] + f[5]) + (f[6] + f[7]))) + f[8];
 }
 
 // ------------------------------------------------------------ forces -------
@@ -202,6 +215,10 @@ __device__ __forceinline__ void external_force(const KParams &kp, int64_t node, 
 template <class R, class Ps>
 __device__ __forceinline__ void stencil_S(const Ps &ps, R &Sx, R &Sy)
 {
+    if constexpr (is_f64<R>()) {
+        f64::stencil_S(ps, Sx, Sy);
+        return;
+    }
     const R p1 = ps(1), p2 = ps(2), p3 = ps(3), p4 = ps(4);
     const R p5 = ps(5), p6 = ps(6), p7 = ps(7), p8 = ps(8);
     const R a = R(1.0 / 3.0), d = R(1.0 / 12.0);
@@ -218,6 +235,10 @@ template <class R>
 __device__ __forceinline__ void collide(const KParams &kp, const R (&f)[9], R rho, R psi, R Sx, R Sy,
                                         R Fex, R Fey, R (&fb)[9], R &ux, R &uy)
 {
+    if constexpr (is_f64<R>()) {
+        f64::collide(kp, f, psi, Sx, Sy, Fex, Fey, fb, ux, uy);
+        return;
+    }
     const R G = R(kp.G);
     const R jx = ((f[1] - f[3]) + (f[5] - f[6])) + (f[8] - f[7]);
     const R jy = ((f[2] - f[4]) + (f[5] + f[6])) - (f[7] + f[8]);
@@ -299,6 +320,10 @@ __device__ __forceinline__ void collide(const KParams &kp, const R (&f)[9], R rh
 template <class R>
 __device__ __forceinline__ void equilibrium(R rho, R ux, R uy, R (&fb)[9])
 {
+    if constexpr (is_f64<R>()) {
+        f64::equilibrium(rho, ux, uy, fb);
+        return;
+    }
     const R u2 = ux * ux + uy * uy;
     const R b1 = rho * (R(-2) + R(3) * u2), b2 = rho * (R(1) - R(3) * u2);
     const R b3 = rho * ux, b4 = -rho * ux, b5 = rho * uy, b6 = -rho * uy;

@@ -20,7 +20,9 @@ struct KParams {
     int per_node_ref;
     // EOS: p = K (rho RT g(rho) - a rho^2); psi = sqrt(two_over_G (p - rho/3))
     double eos_a, eos_b, eos_RT, eos_K, two_over_G;
+    double eos_R, eos_T;  // raw R and T (FP64 path evaluates (rho R) T like a plain formula)
     double G;
+    double k1, k2;        // raw source coefficients (FP64 path)
     // source term with G folded in (|F_int|^2/(G psi^2) = G |S|^2, S = F_int/(-G psi)):
     // Q1 = kq1 |S|^2, Q2 = q2fac Q1, Q7 = kq7 (Sx^2 - Sy^2), Q8 = kq7 Sx Sy,
     // Q4 = (c1G Sx^2 - c2G Sy^2) ux, Q6 = (c1G Sy^2 - c2G Sx^2) uy

@@ -129,6 +129,9 @@ class Simulation:
     """One lattice on the current CUDA device (owns an lbm_ctx)."""
 
     def __init__(self, params=None, stream=None, **overrides):
+        """params: LbmParams (see default_params); stream: torch.cuda.Stream, a raw
+        cudaStream_t handle, or None for a stream owned by the library.  torch's default
+        stream maps to the legacy default stream so torch events order with the steps."""
         self.lib = load_library()
         if params is None:
             params = default_params(**overrides)
@@ -138,10 +141,13 @@ class Simulation:
         self.params = params
         self.nx, self.ny = params.nx, params.ny
         self.n = self.nx * self.ny
-        if stream is not None and hasattr(stream, "cuda_stream"):
-            stream = stream.cuda_stream
+        handle = None
+        if stream is not None:
+            handle = stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+            if handle == 0:
+                handle = 1  # the legacy default stream (cudaStreamLegacy), torch's default stream
         h = _vp()
-        st = self.lib.lbm_create(ctypes.byref(params), _vp(stream) if stream else None, ctypes.byref(h))
+        st = self.lib.lbm_create(ctypes.byref(params), _vp(handle) if handle else None, ctypes.byref(h))
         if st != 0:
             raise LbmError(st, self.lib.lbm_last_error(None).decode())
         self._h = h

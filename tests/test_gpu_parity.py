@@ -74,7 +74,7 @@ def test_diagnostics_match_oracle(name, oracle_runs):
     do = oracle_runs[name].diagnostics()
     scale = np.array([do[0], do[0], do[0], abs(do[3]) + abs(do[4]) + 1e-30, abs(do[3]) + abs(do[4]) + 1e-30,
                       abs(do[5]) + abs(do[6]) + 1e-30, abs(do[5]) + abs(do[6]) + 1e-30,
-                      abs(do[7]) + 1e-30, do[8] + 1e-30, do[9]])
+                      do[8] * do[9] + 1e-30, do[8] + 1e-30, do[9]])
     err = np.abs(dg - do) / scale
     assert err[[0, 8, 9]].max() < 1e-10, (dg, do)
     assert err[[1, 2, 3, 4, 5, 6, 7]].max() < 1e-7, (dg, do)
