@@ -207,7 +207,7 @@ static bool fused_possible(const lbm_ctx *c)
     const lbm_params &p = c->p;
     if (c->solid || c->q || c->wall_u) return false;
     if (c->L.fused_align <= 0 || p.nx % c->L.fused_align != 0) return false;
-    if (p.nx < c->L.fused_tile_x / 4 || p.ny < 4) return false;
+    if (p.nx < 2 * c->L.fused_tile_x || p.ny < 4) return false;
     return true;
 }
 

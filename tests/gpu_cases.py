@@ -76,15 +76,17 @@ def cases():
     p = cs_params(nx=n, ny=n, periodic_x=True, periodic_y=True, Fx=f / math.sqrt(2), Fy=f / math.sqrt(2),
                   tau_l=1.0, tau_g=0.55, scheme=1)
     out["oblique"] = Case("oblique", p, I.oblique_slab(n, rl, rg, 14), 500, solid=I.oblique_band_walls(n))
-    n = 48
-    solid, wall_u, q = I.annulus(n, n, 7.3, 21.6, u_wall_out=0.01)
-    rho = np.where(solid == 1, rg, I.droplet(n, n, rl, rg, 14.0, (n - 1) / 2, (n - 1) / 2, periodic_y=False))
+    n = 64
+    solid, wall_u, q = I.annulus(n, n, 8.3, 29.6, u_wall_out=0.01)
+    c0 = (n - 1) / 2
+    r = np.hypot(np.arange(n)[None, :] - c0, np.arange(n)[:, None] - c0)
+    ring = rg + 0.5 * (rl - rg) * (np.tanh(2 * (r - 14.0) / 4.0) - np.tanh(2 * (r - 22.0) / 4.0))
     p = cs_params(nx=n, ny=n, periodic_x=True, periodic_y=True, scheme=1)
-    out["annulus"] = Case("annulus", p, rho, 150, solid=solid, wall_u=wall_u, q=q)
+    out["annulus"] = Case("annulus", p, np.where(solid == 1, rg, ring), 250, solid=solid, wall_u=wall_u, q=q)
     p = cs_params(nx=37, ny=23, periodic_x=True, periodic_y=False, Fx=3e-6, Fy=1e-6, scheme=0)
     out["ragged"] = Case("ragged", p, I.droplet(37, 23, rl, rg, 6, 17.2, 11.0, periodic_x=True), 250)
     p = cs_params(nx=1, ny=5, periodic_x=True, periodic_y=True, scheme=1)
-    out["tiny"] = Case("tiny", p, np.linspace(0.05, 0.3, 5).reshape(5, 1), 50)
+    out["tiny"] = Case("tiny", p, (0.15 + 0.05 * np.sin(2 * np.pi * np.arange(5) / 5)).reshape(5, 1), 50)
     return out
 
 

@@ -1,0 +1,93 @@
+"""The fused single-pass kernel against the two-pass kernel (bit-identical populations,
+every storage precision, periodic and walled edges, partial strips and segments), and
+against the FP64 oracle on sampled nodes at the full benchmark size."""
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_2604_13407_gb300 import inputs as I
+from paper_2604_13407_gb300 import lbm
+from tests import gpu_cases as GC
+from tests.setups import cs_case, cs_params
+
+pytestmark = pytest.mark.gpu
+
+PRECS = [(lbm.F64, {}), (lbm.F32, {}), (lbm.F16DEV, {}), (lbm.F16DEV, {"per_node_ref": 1}),
+         (lbm.BF16DEV, {"per_node_ref": 1})]
+
+
+def geometries():
+    T, rg, rl = cs_case()
+    g = {}
+    p = cs_params(nx=256, ny=64, periodic_x=True, periodic_y=True, force_mode=1, Fy=-2e-5)
+    g["periodic"] = GC.Case("periodic", p, I.droplet(256, 64, rl, rg, 12, 100.3, 30.2, periodic_x=True), 60)
+    p = cs_params(nx=264, ny=37, periodic_x=True, periodic_y=False, Fx=2e-6)
+    g["walls_y_ragged"] = GC.Case("walls_y_ragged", p, I.tanh_slab(264, 37, rl, rg, 15), 60)
+    p = cs_params(nx=272, ny=96, periodic_x=False, periodic_y=True, force_mode=1, Fy=-1e-5)
+    g["walls_x"] = GC.Case("walls_x", p, I.droplet(272, 96, rl, rg, 14, 135.6, 60.1, periodic_x=False), 60)
+    return g
+
+
+GEOMS = geometries()
+
+
+@pytest.mark.parametrize("prec,kw", PRECS)
+@pytest.mark.parametrize("geom", sorted(GEOMS))
+def test_fused_equals_two_pass(geom, prec, kw):
+    c = GEOMS[geom]
+    a = GC.run_gpu(c, prec, lbm.KERNEL_TWO_PASS, **kw)
+    b = GC.run_gpu(c, prec, lbm.KERNEL_FUSED, **kw)
+    assert a.kernel_in_use == lbm.KERNEL_TWO_PASS and b.kernel_in_use == lbm.KERNEL_FUSED
+    assert np.array_equal(a.get_state(), b.get_state())
+    assert np.array_equal(a.save_state(), b.save_state())
+
+
+def test_fused_fp64_matches_oracle():
+    c = GEOMS["walls_x"]
+    o = GC.run_oracle(c)
+    g = GC.run_gpu(c, lbm.F64, lbm.KERNEL_FUSED)
+    assert g.kernel_in_use == lbm.KERNEL_FUSED
+    e_rho, e_u = GC.field_errors(g, o)
+    assert e_rho < 1e-10 and e_u < 1e-10, (e_rho, e_u)
+
+
+def _patch(A, cx, cy, r=2):
+    ny, nx = A.shape[1:]
+    ys = [(cy + d) % ny for d in range(-r, r + 1)]
+    xs = [(cx + d) % nx for d in range(-r, r + 1)]
+    return A[:, ys][:, :, xs]
+
+
+@pytest.mark.parametrize("prec,tol", [(lbm.F32, 2e-6), (lbm.F16DEV, 2e-3)])
+def test_full_size_sampled_nodes_match_oracle(prec, tol):
+    """8192 x 8192 periodic spinodal workload in the launch configuration bench.py times:
+    the update of sampled nodes is recomputed by the oracle from the GPU's previous state
+    (a 5 x 5 patch holds everything one node update depends on)."""
+    import torch
+    import bench
+    n = 8192
+    sim = bench.make_sim(n, prec)
+    assert sim.kernel_in_use == lbm.KERNEL_FUSED
+    sim.init_fields(bench.workload_rho(n))
+    sim.step(3)
+    before = torch.empty((9, n, n), dtype=torch.float64, device="cuda")
+    sim.get_state(before)
+    rng = np.random.default_rng(11)
+    pts = [(0, 0), (n - 1, n - 1), (127, 4095), (128, 1), (n - 1, 0)] + [tuple(rng.integers(0, n, 2)) for _ in range(12)]
+    patches = []
+    for cx, cy in pts:
+        ys = torch.tensor([(cy + d) % n for d in range(-2, 3)], device="cuda")
+        xs = torch.tensor([(cx + d) % n for d in range(-2, 3)], device="cuda")
+        patches.append(before.index_select(1, ys).index_select(2, xs).cpu().numpy())
+    sim.step(1)
+    sim.get_state(before)
+    after = [before[:, cy, cx].cpu().numpy() for cx, cy in pts]
+    del before
+    p = O.Params(nx=5, ny=5, periodic_x=False, periodic_y=False, scheme=1, T=bench.T_07,
+                 rho_l=bench.RHO_L, rho_g=bench.RHO_G, rho_s=bench.RHO_G)
+    for P, a in zip(patches, after):
+        s = O.OracleSim(p)
+        s.set_state(P)
+        s.step(1)
+        ref = s.get_state()[:, 2, 2]
+        assert np.abs(a - ref).max() < tol * np.abs(ref).max(), (a, ref)
