@@ -1,7 +1,8 @@
 """Throughput of the D2Q9 pseudopotential MRT step on the periodic spinodal workload.
 
 Workload: 8192 x 8192 periodic lattice, Carnahan-Starling EOS (a = 1, b = 4, R = 1,
-T = 0.7 T_c), epsilon = 1.895, improved third-order source, tau = 0.8, initial density
+T = 0.7 T_c), epsilon = 1.895, improved third-order source, tau = 1.0 (at tau = 0.8 the
+spinodal transient reaches |u| ~ 0.26 and is marginally stable), initial density
 rho = (rho_l + rho_g)/2 (1 + U(-0.01, 0.01)) with SplitMix64 seed 5, u = 0.  One step is
 one lattice update of every node.  Inputs (two 2.4 GB population buffers in FP32) are
 far larger than the 129 MB L2, so no flush is needed between steps.
@@ -26,6 +27,7 @@ sys.path.insert(0, ROOT)
 
 RHO_G, RHO_L = 0.009291723294794338, 0.3581443962580134  # Maxwell densities of the EOS at 0.7 T_c
 T_07 = 0.7 * 0.3773 / 4.0
+TAU = 1.0
 BYTES = {"f64": 144, "f32": 72, "f16dev": 36, "bf16dev": 36}
 HBM_FALLBACK = 6800.0
 
@@ -114,10 +116,11 @@ def make_sim(n, precision, scheme=1, kernel=0, per_node_ref=0):
     from paper_2604_13407_gb300 import lbm
     # FP16 deviations stay below 2^-4 (global reference = mean density) or 2^-9 (per-node
     # reference); the 2^k scale moves them out of the FP16 subnormal range.
-    scale = (20 if per_node_ref else 19) if precision == lbm.F16DEV else 0
+    scale = (18 if per_node_ref else 19) if precision == lbm.F16DEV else 0
     p = lbm.default_params(nx=n, ny=n, periodic_x=1, periodic_y=1, precision=precision, scheme=scheme,
                            kernel=kernel, per_node_ref=per_node_ref, T=T_07, rho_l=RHO_L, rho_g=RHO_G,
-                           rho_s=RHO_G, rho_ref=0.5 * (RHO_L + RHO_G), storage_scale_log2=scale)
+                           rho_s=RHO_G, rho_ref=0.5 * (RHO_L + RHO_G), storage_scale_log2=scale,
+                           tau_l=TAU, tau_g=TAU)
     return lbm.Simulation(p, stream=torch.cuda.current_stream())
 
 
@@ -188,7 +191,7 @@ def oracle_glups(n, seconds_target=10.0, max_steps=50):
     """The FP64 oracle on an n x n sample of the workload; returns (GLUPS, steps, threads)."""
     from oracle import oracle as O
     p = O.Params(nx=n, ny=n, periodic_x=True, periodic_y=True, scheme=1, T=T_07, rho_l=RHO_L,
-                 rho_g=RHO_G, rho_s=RHO_G)
+                 rho_g=RHO_G, rho_s=RHO_G, tau_l=TAU, tau_g=TAU)
     s = O.OracleSim(p)
     s.init(workload_rho(n))
     t0 = time.perf_counter()
@@ -209,7 +212,7 @@ def run_reference(args):
     n = args.ref_sample
     from oracle import oracle as O
     p = O.Params(nx=n, ny=n, periodic_x=True, periodic_y=True, scheme=1, T=T_07, rho_l=RHO_L,
-                 rho_g=RHO_G, rho_s=RHO_G)
+                 rho_g=RHO_G, rho_s=RHO_G, tau_l=TAU, tau_g=TAU)
     s = O.OracleSim(p)
     s.init(workload_rho(n))
     s.step(args.warmup)
@@ -241,6 +244,7 @@ def main():
     ap.add_argument("--variants", type=int, default=1, help="also time the other precisions / scheme")
     ap.add_argument("--cpu-baseline", type=int, default=1)
     ap.add_argument("--ref-sample", type=int, default=512)
+    ap.add_argument("--e2e", type=int, default=1)
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -300,7 +304,7 @@ def main():
             s2.close()
 
     e2e = None
-    if rank == 0:
+    if rank == 0 and args.e2e:
         ev, hb, db = e2e_glups(n, prec_id[args.precision], args.steps, rho)
         e2e = {"value": ev, "unit": "GLUPS", "h2d_bytes_per_step": hb, "d2h_bytes_per_step": db}
     cpu = None

@@ -34,12 +34,38 @@ GEOMS = geometries()
 @pytest.mark.parametrize("prec,kw", PRECS)
 @pytest.mark.parametrize("geom", sorted(GEOMS))
 def test_fused_equals_two_pass(geom, prec, kw):
+    """FP64 (compiled without multiply-add contraction): bit-identical.  Other precisions:
+    the compiler contracts multiply-adds differently in the two inlined copies of the
+    collision, so they agree to rounding; a staging or synchronisation fault would give
+    O(1) differences."""
     c = GEOMS[geom]
     a = GC.run_gpu(c, prec, lbm.KERNEL_TWO_PASS, **kw)
     b = GC.run_gpu(c, prec, lbm.KERNEL_FUSED, **kw)
     assert a.kernel_in_use == lbm.KERNEL_TWO_PASS and b.kernel_in_use == lbm.KERNEL_FUSED
-    assert np.array_equal(a.get_state(), b.get_state())
-    assert np.array_equal(a.save_state(), b.save_state())
+    A, B = a.get_state(), b.get_state()
+    if prec == lbm.F64:
+        assert np.array_equal(A, B)
+        assert a.save_state() == b.save_state()
+    else:
+        tol = 1e-5 if prec == lbm.F32 else 2e-3
+        assert np.all(np.isfinite(B))
+        assert np.abs(A - B).max() < tol * np.abs(A).max(), np.abs(A - B).max() / np.abs(A).max()
+
+
+@pytest.mark.parametrize("prec,kw", PRECS)
+def test_fused_one_step_equals_two_pass(prec, kw):
+    """From one shared state, one fused step and one two-pass step agree to a few ulps."""
+    c = GEOMS["walls_y_ragged"]
+    base = GC.run_gpu(c, prec, lbm.KERNEL_TWO_PASS, steps=25, **kw)
+    A0 = base.get_state()
+    out = []
+    for kernel in (lbm.KERNEL_TWO_PASS, lbm.KERNEL_FUSED):
+        s = lbm.Simulation(GC.gpu_params(c.params, prec, kernel, **kw))
+        s.set_state(A0)
+        s.step(1)
+        out.append(s.get_state())
+    tol = 0.0 if prec == lbm.F64 else (1e-6 if prec == lbm.F32 else 1e-3)
+    assert np.abs(out[0] - out[1]).max() <= tol * np.abs(out[0]).max()
 
 
 def test_fused_fp64_matches_oracle():
@@ -84,7 +110,7 @@ def test_full_size_sampled_nodes_match_oracle(prec, tol):
     after = [before[:, cy, cx].cpu().numpy() for cx, cy in pts]
     del before
     p = O.Params(nx=5, ny=5, periodic_x=False, periodic_y=False, scheme=1, T=bench.T_07,
-                 rho_l=bench.RHO_L, rho_g=bench.RHO_G, rho_s=bench.RHO_G)
+                 rho_l=bench.RHO_L, rho_g=bench.RHO_G, rho_s=bench.RHO_G, tau_l=bench.TAU, tau_g=bench.TAU)
     for P, a in zip(patches, after):
         s = O.OracleSim(p)
         s.set_state(P)
