@@ -9,13 +9,13 @@ Launchers launchers_bf16()
     Launchers L{};
     L.psi_pass = &TwoPass<__nv_bfloat16>::psi_pass;
     L.collide_pass = &TwoPass<__nv_bfloat16>::collide_pass;
-    L.fused_pass = &Fused<__nv_bfloat16, 128, 8>::launch;
+    L.fused_pass = &Fused<__nv_bfloat16, 4, 8>::launch;
     L.init = &TwoPass<__nv_bfloat16>::init;
     L.moments = &TwoPass<__nv_bfloat16>::moments;
     L.diag = &TwoPass<__nv_bfloat16>::diag;
     L.get_state = &TwoPass<__nv_bfloat16>::get_state;
     L.set_state = &TwoPass<__nv_bfloat16>::set_state;
-    L.fused_tile_x = 128;
+    L.fused_tile_x = FusedLayout<__nv_bfloat16, 4, 8>::TX;
     L.fused_align = FusedGeom<__nv_bfloat16>::HX;
     return L;
 }

@@ -9,13 +9,13 @@ Launchers launchers_f16()
     Launchers L{};
     L.psi_pass = &TwoPass<__half>::psi_pass;
     L.collide_pass = &TwoPass<__half>::collide_pass;
-    L.fused_pass = &Fused<__half, 128, 8>::launch;
+    L.fused_pass = &Fused<__half, 4, 8>::launch;
     L.init = &TwoPass<__half>::init;
     L.moments = &TwoPass<__half>::moments;
     L.diag = &TwoPass<__half>::diag;
     L.get_state = &TwoPass<__half>::get_state;
     L.set_state = &TwoPass<__half>::set_state;
-    L.fused_tile_x = 128;
+    L.fused_tile_x = FusedLayout<__half, 4, 8>::TX;
     L.fused_align = FusedGeom<__half>::HX;
     return L;
 }

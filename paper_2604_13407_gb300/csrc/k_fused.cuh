@@ -1,19 +1,25 @@
-// Fused single-pass step: one CTA owns a strip of TX columns and walks down a segment of
-// rows.  Each lattice row of the nine population planes (plus the reference-density plane
-// of per-node FP16/BF16 storage) is brought into a shared-memory ring by bulk async
-// copies (the TMA engine, cp.async.bulk) that complete on one mbarrier per ring slot,
-// several rows ahead of use.  For every row the CTA computes rho and psi on the strip
-// plus a one-node halo from the staged populations, then pulls, collides and stores the
-// strip row with coalesced stores.  Halo psi is recomputed instead of being written and
-// re-read, so HBM sees each population read once and written once (72 B per update in
-// FP32, 36 B in FP16/BF16).
+// Fused single-pass step, warp-specialised.  A CTA owns a strip of 30 NW columns and
+// walks down a segment of rows.  One producer warp stages each lattice row of the nine
+// population planes (plus the reference-density plane of per-node FP16/BF16 storage)
+// into a shared-memory ring with bulk async copies (the TMA engine, cp.async.bulk); each
+// ring slot has a "full" mbarrier (completed by the copies' byte count) and an "empty"
+// mbarrier (one arrival per consumer warp).  Each of the NW consumer warps owns 32
+// consecutive columns: its lanes pull the populations of their node of row r, form rho
+// and psi, and keep the pulled populations in registers; one row later, lanes 1..30
+// collide their node of row r - 1 with the psi of the 3 x 3 neighbourhood taken from the
+// last three psi rows in registers and from neighbouring lanes by warp shuffles (lanes 0
+// and 31 supply the halo columns).  There is no block-wide barrier in the loop: warps
+// advance independently, limited only by the ring.  Halo psi is recomputed rather than
+// written and re-read, so HBM sees each population read once and written once (72 B per
+// update in FP32, 36 B in FP16/BF16).
 //
 // The kernel calls the same pull, density, pseudopotential, stencil and collision
 // functions as the two-pass step, so both give bit-identical populations.  Supported
 // geometry: periodic directions and half-way walls just outside non-periodic edges (no
 // solid mask, no moving or interpolated walls); nx a multiple of the 16-byte column
-// group and at least 2 TX.  Every mbarrier wait is bounded; a wait that runs out sets
-// DERR_TIMEOUT in the device error word and the CTA returns after a bounded drain.
+// group and at least twice the strip width.  Every mbarrier wait is bounded; a wait that
+// runs out sets DERR_TIMEOUT in the device error word and the warp leaves its loop; the
+// producer drains the copies in flight (again bounded) before the CTA exits.
 #pragma once
 
 #include "lbm_device.cuh"
@@ -70,41 +76,31 @@ struct FusedGeom {
     static constexpr int HX = (16 / (int)sizeof(S)) < 2 ? 2 : 16 / (int)sizeof(S);  // halo columns, one 16 B group
 };
 
-template <class S, int TX, int RING>
+template <class S, int NW, int RING>
 struct FusedLayout {
     typedef typename Codec<S>::R R;
+    static constexpr int TX = 30 * NW;                          // output columns per strip
     static constexpr int HX = FusedGeom<S>::HX;
     static constexpr int W = TX + 2 * HX;                      // staged columns per row
     static constexpr int POP_ROW = 9 * W * (int)sizeof(S);     // bytes of one staged row (9 planes)
     static constexpr int REF_ROW = W * 4;                      // bytes of one staged reference row
-    static constexpr int PSI_ROW = ((TX + 2) * (int)sizeof(R) + 15) / 16 * 16;
-    static size_t bytes(bool ref)
-    {
-        return (size_t)RING * POP_ROW + (ref ? (size_t)RING * REF_ROW : 0) + 4 * (size_t)PSI_ROW + RING * 8 + 16;
-    }
+    static size_t bytes(bool ref) { return (size_t)RING * POP_ROW + (ref ? (size_t)RING * REF_ROW : 0) + 2 * RING * 8 + 16; }
 };
 
-// Reads population k of node (x, y) from the staged ring.  (x, y) are wrapped domain
-// coordinates within one node of the node being processed (cx, cy).
-template <class S, int TX, int RING>
+// Reads population k of the staged node at (col, row slot) -- col is the staged column.
+template <class S, int NW, int RING>
 struct RingAt {
     typedef typename Codec<S>::R R;
-    typedef FusedLayout<S, TX, RING> L;
+    typedef FusedLayout<S, NW, RING> L;
     const KParams &kp;
-    const unsigned char *pops;  // ring base
-    const float *refs;          // reference ring base (per-node ref) or null
-    int x_lo;                   // global column of staged column 0 (unwrapped)
-    int first;                  // first staged row
-    int cx, cy;                 // unwrapped coordinates of the node being processed
+    const unsigned char *pops;
+    const float *refs;
+    int x_lo, first;
+    // (x, y): unwrapped coordinates within one node of the node being pulled
     __device__ __forceinline__ R operator()(int k, int x, int y) const
     {
-        int dx = x - cx, dy = y - cy;
-        if (dx > 1) dx -= kp.nx;
-        if (dx < -1) dx += kp.nx;
-        if (dy > 1) dy -= kp.ny;
-        if (dy < -1) dy += kp.ny;
-        const int col = cx + dx - x_lo;
-        const int slot = (cy + dy - first) & (RING - 1);
+        const int col = x - x_lo;
+        const int slot = (y - first) & (RING - 1);
         const S *row = reinterpret_cast<const S *>(pops + (size_t)slot * L::POP_ROW) + k * L::W;
         R wref = R(0);
         if (IsDev<S>::value) wref = w_<R>(k) * (kp.per_node_ref ? R(refs[slot * L::W + col]) : R(kp.rho_ref));
@@ -114,182 +110,195 @@ struct RingAt {
 
 // Pull of node (cx, cy) (unwrapped column, row) from the ring: plain copies, or half-way
 // bounce-back when the source lies beyond a non-periodic edge.
-template <class R, class At>
+template <bool PERIODIC, class R, class At>
 __device__ __forceinline__ void pull_ring(const KParams &kp, int cx, int cy, const At &at, R (&f)[9])
 {
 #pragma unroll
     for (int i = 0; i < 9; ++i) {
         const int xs = cx - ex_(i), ys = cy - ey_(i);
-        const bool wall = (!kp.periodic_x && (xs < 0 || xs >= kp.nx)) || (!kp.periodic_y && (ys < 0 || ys >= kp.ny));
+        bool wall = false;
+        if (!PERIODIC)
+            wall = (!kp.periodic_x && (xs < 0 || xs >= kp.nx)) || (!kp.periodic_y && (ys < 0 || ys >= kp.ny));
         if (i == 0 || !wall) f[i] = at(i, xs, ys);
         else f[i] = at(opp_(i), cx, cy) + R(0);  // same arithmetic as bounce() with q = 1/2, u_w = 0
     }
 }
 
-template <class S, int TX, int RING>
-__global__ void __launch_bounds__(TX) k_fused(KParams kp, int seg_rows)
+template <class S, int NW, int RING, bool PERIODIC>
+__global__ void __launch_bounds__(32 * (NW + 1)) k_fused(KParams kp, int seg_rows)
 {
     typedef typename Codec<S>::R R;
-    typedef FusedLayout<S, TX, RING> L;
-    constexpr int HX = L::HX, W = L::W;
+    typedef FusedLayout<S, NW, RING> L;
+    constexpr int TX = L::TX, HX = L::HX, W = L::W;
     extern __shared__ __align__(128) unsigned char smem[];
     unsigned char *pops = smem;
     float *refs = kp.per_node_ref ? reinterpret_cast<float *>(smem + (size_t)RING * L::POP_ROW) : nullptr;
-    unsigned char *psi_base = smem + (size_t)RING * L::POP_ROW + (kp.per_node_ref ? (size_t)RING * L::REF_ROW : 0);
-    uint64_t *bars = reinterpret_cast<uint64_t *>(psi_base + 4 * L::PSI_ROW);
-    int *abort_flag = reinterpret_cast<int *>(bars + RING);
+    uint64_t *full = reinterpret_cast<uint64_t *>(smem + (size_t)RING * L::POP_ROW +
+                                                  (kp.per_node_ref ? (size_t)RING * L::REF_ROW : 0));
+    uint64_t *empty = full + RING;
 
-    const int t = threadIdx.x;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int nx = kp.nx, ny = kp.ny;
     const int x0 = blockIdx.x * TX;
     const int yb = blockIdx.y * seg_rows;
     const int ye = min(yb + seg_rows, ny);
     const int first = yb - 2, last = ye + 1;  // staged rows
     const int x_lo = x0 - HX;
-    const S *A = static_cast<const S *>(kp.src);
 
-    if (t == 0) {
-        for (int s = 0; s < RING; ++s) mbar_init(bars + s, 1);
-        *abort_flag = 0;
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < RING; ++s) {
+            mbar_init(full + s, 1);
+            mbar_init(empty + s, NW);
+        }
         fence_mbar_init();
         fence_proxy_async();
     }
     __syncthreads();
 
-    // Stage row r (all planes) into its ring slot; rows beyond a non-periodic edge are
-    // not loaded, their slot barrier just completes.
-    auto issue = [&](int r) {
-        const int slot = (r - first) & (RING - 1);
-        uint64_t *bar = bars + slot;
-        int gy = r;
-        if (gy < 0 || gy >= ny) {
-            if (!kp.periodic_y) {
-                mbar_arrive(bar);
-                return;
+    if (warp == NW) {
+        // ------------------------------------------------------ producer warp
+        if (lane != 0) return;
+        const S *A = static_cast<const S *>(kp.src);
+        int r = first;
+        for (; r <= last; ++r) {
+            const int slot = (r - first) & (RING - 1);
+            const int use = (r - first) / RING;
+            if (use > 0 && !mbar_wait_bounded(empty + slot, (uint32_t)((use - 1) & 1))) {
+                atomicOr(kp.err, DERR_TIMEOUT);
+                break;
             }
-            gy = ((gy % ny) + ny) % ny;
+            uint64_t *bar = full + slot;
+            int gy = r;
+            if (gy < 0 || gy >= ny) {
+                if (!kp.periodic_y) {
+                    mbar_arrive(bar);
+                    continue;
+                }
+                gy = ((gy % ny) + ny) % ny;
+            }
+            int sx[3], dx[3], cnt[3], nseg = 0;
+            const int lo = x_lo, hi = x0 + TX + HX;
+            const int m0 = lo < 0 ? 0 : lo, m1 = hi > nx ? nx : hi;
+            sx[nseg] = m0, dx[nseg] = m0 - lo, cnt[nseg] = m1 - m0, ++nseg;
+            if (lo < 0 && kp.periodic_x) sx[nseg] = nx + lo, dx[nseg] = 0, cnt[nseg] = -lo, ++nseg;
+            if (hi > nx && kp.periodic_x) sx[nseg] = 0, dx[nseg] = nx - lo, cnt[nseg] = hi - nx, ++nseg;
+            uint32_t cols = 0;
+            for (int q = 0; q < nseg; ++q) cols += cnt[q];
+            fence_proxy_async();
+            mbar_expect_tx(bar, cols * (9u * (uint32_t)sizeof(S) + (refs ? 4u : 0u)));
+            unsigned char *prow = pops + (size_t)slot * L::POP_ROW;
+            for (int i = 0; i < 9; ++i) {
+                const S *src = A + i * kp.plane + (int64_t)gy * kp.pitch;
+                S *dst = reinterpret_cast<S *>(prow) + i * W;
+                for (int q = 0; q < nseg; ++q) bulk_g2s(dst + dx[q], src + sx[q], cnt[q] * (uint32_t)sizeof(S), bar);
+            }
+            if (refs) {
+                const float *src = kp.ref_src + (int64_t)gy * kp.pitch;
+                float *dst = refs + slot * W;
+                for (int q = 0; q < nseg; ++q) bulk_g2s(dst + dx[q], src + sx[q], cnt[q] * 4u, bar);
+            }
         }
-        int sx[3], dx[3], cnt[3], nseg = 0;
-        const int lo = x_lo, hi = x0 + TX + HX;
-        const int m0 = lo < 0 ? 0 : lo, m1 = hi > nx ? nx : hi;
-        sx[nseg] = m0, dx[nseg] = m0 - lo, cnt[nseg] = m1 - m0, ++nseg;
-        if (lo < 0 && kp.periodic_x) sx[nseg] = nx + lo, dx[nseg] = 0, cnt[nseg] = -lo, ++nseg;
-        if (hi > nx && kp.periodic_x) sx[nseg] = 0, dx[nseg] = nx - lo, cnt[nseg] = hi - nx, ++nseg;
-        uint32_t cols = 0;
-        for (int s = 0; s < nseg; ++s) cols += cnt[s];
-        const uint32_t bytes = cols * (9u * (uint32_t)sizeof(S) + (refs ? 4u : 0u));
-        mbar_expect_tx(bar, bytes);
-        unsigned char *prow = pops + (size_t)slot * L::POP_ROW;
-        for (int i = 0; i < 9; ++i) {
-            const S *src = A + i * kp.plane + (int64_t)gy * kp.pitch;
-            S *dst = reinterpret_cast<S *>(prow) + i * W;
-            for (int s = 0; s < nseg; ++s) bulk_g2s(dst + dx[s], src + sx[s], cnt[s] * (uint32_t)sizeof(S), bar);
-        }
-        if (refs) {
-            const float *src = kp.ref_src + (int64_t)gy * kp.pitch;
-            float *dst = refs + slot * W;
-            for (int s = 0; s < nseg; ++s) bulk_g2s(dst + dx[s], src + sx[s], cnt[s] * 4u, bar);
-        }
-    };
-    auto parity_of = [&](int r) -> uint32_t { return (uint32_t)(((r - first) / RING) & 1); };
-    auto wait_row = [&](int r) -> bool { return mbar_wait_bounded(bars + ((r - first) & (RING - 1)), parity_of(r)); };
+        // drain: every issued row must have landed before the CTA may exit
+        for (int q = max(first, r - RING); q < r && q <= last; ++q)
+            mbar_wait_bounded(full + ((q - first) & (RING - 1)), (uint32_t)(((q - first) / RING) & 1));
+        return;
+    }
 
-    if (t == 0)
-        for (int r = first; r <= last && r < first + RING; ++r) issue(r);
-
+    // ----------------------------------------------------------- consumer warps
+    const RingAt<S, NW, RING> at{kp, pops, refs, x_lo, first};
+    const int col = x0 + 30 * warp - 1 + lane;  // unwrapped column of this lane's node
+    const bool col_out = !PERIODIC && !kp.periodic_x && (col < 0 || col >= nx);
+    const bool collides = lane >= 1 && lane <= 30 && col < nx;
     const R psi_s = R(kp.psi_s);
-    bool ok = true;
+    R f_old[9], rho_old = R(0), psi_m2 = psi_s, psi_m1 = psi_s;
+#pragma unroll
+    for (int i = 0; i < 9; ++i) f_old[i] = R(0);
+    // every lane polls; the outcome is made warp-uniform so that the shuffles below never
+    // run in a partially exited warp
+    auto wait_full = [&](int r) -> bool {
+        const bool got = mbar_wait_bounded(full + ((r - first) & (RING - 1)), (uint32_t)(((r - first) / RING) & 1));
+        return __all_sync(0xffffffffu, got);
+    };
+    bool ok = wait_full(first) && wait_full(first + 1);
     for (int rp = yb - 1; rp <= ye && ok; ++rp) {
-        // rows rp - 1 .. rp + 1 must be staged (earlier ones were waited for already)
-        bool good = true;
-        if (rp == yb - 1) good = wait_row(rp - 1) && wait_row(rp);
-        good = good && wait_row(rp + 1);
-        if (!good) *abort_flag = 1;
-
-        // psi of row rp over columns x0 - 1 .. x0 + TX
-        R *psi_row = reinterpret_cast<R *>(psi_base + ((rp - first) & 3) * L::PSI_ROW);
-        for (int c = t; c < TX + 2; c += TX) {
-            const int gx = x0 - 1 + c;
-            const bool outside = (!kp.periodic_x && (gx < 0 || gx >= nx)) || (!kp.periodic_y && (rp < 0 || rp >= ny));
-            R v = psi_s;
-            if (!outside && good) {
-                R f[9];
-                pull_ring<R>(kp, gx, rp, RingAt<S, TX, RING>{kp, pops, refs, x_lo, first, gx, rp}, f);
-                v = psi_of<R>(kp, density<R>(f));
-            }
-            psi_row[c] = v;
-        }
-        __syncthreads();
-        if (*abort_flag) {
+        if (!wait_full(rp + 1)) {
             ok = false;
             break;
         }
-        // collide row y = rp - 1
+        // pull, rho, psi of node (col, rp)
+        const bool row_out = !PERIODIC && !kp.periodic_y && (rp < 0 || rp >= ny);
+        R f_new[9], rho_new = R(0), psi_new = psi_s;
+#pragma unroll
+        for (int i = 0; i < 9; ++i) f_new[i] = R(0);
+        if (!col_out && !row_out) {
+            pull_ring<PERIODIC, R>(kp, col, rp, at, f_new);
+            rho_new = density<R>(f_new);
+            psi_new = psi_of<R>(kp, rho_new);
+        }
+        __syncwarp();
+        // row rp - 1 is not needed any more by this warp
+        if (lane == 0 && rp - 1 >= first) mbar_arrive(empty + ((rp - 1 - first) & (RING - 1)));
+        // psi of the neighbour columns from the adjacent lanes
+        const R a_m2 = __shfl_up_sync(0xffffffffu, psi_m2, 1), b_m2 = __shfl_down_sync(0xffffffffu, psi_m2, 1);
+        const R a_m1 = __shfl_up_sync(0xffffffffu, psi_m1, 1), b_m1 = __shfl_down_sync(0xffffffffu, psi_m1, 1);
+        const R a_p0 = __shfl_up_sync(0xffffffffu, psi_new, 1), b_p0 = __shfl_down_sync(0xffffffffu, psi_new, 1);
         const int y = rp - 1;
-        const int x = x0 + t;
-        if (y >= yb && x < nx) {
-            const R *p0 = reinterpret_cast<const R *>(psi_base + ((y - 1 - first) & 3) * L::PSI_ROW);
-            const R *p1 = reinterpret_cast<const R *>(psi_base + ((y - first) & 3) * L::PSI_ROW);
-            const R *p2 = reinterpret_cast<const R *>(psi_base + ((y + 1 - first) & 3) * L::PSI_ROW);
-            const int c = t + 1;
+        if (collides && y >= yb) {
+            // neighbour psi along e_i: rows y-1 (m2), y (m1), y+1 (new); columns -1 (a), +1 (b)
             auto ps = [&](int i) -> R {
                 const int dxn = ex_(i), dyn = ey_(i);
-                const R *row = dyn < 0 ? p0 : (dyn > 0 ? p2 : p1);
-                return row[c + dxn];
+                if (dyn < 0) return dxn < 0 ? a_m2 : (dxn > 0 ? b_m2 : psi_m2);
+                if (dyn > 0) return dxn < 0 ? a_p0 : (dxn > 0 ? b_p0 : psi_new);
+                return dxn < 0 ? a_m1 : b_m1;
             };
-            R f[9], fb[9], Sx, Sy, Fex, Fey, ux, uy;
-            pull_ring<R>(kp, x, y, RingAt<S, TX, RING>{kp, pops, refs, x_lo, first, x, y}, f);
-            const R rho = density<R>(f);
+            R fb[9], Sx, Sy, Fex, Fey, ux, uy;
             stencil_S<R>(ps, Sx, Sy);
-            external_force<R>(kp, (int64_t)y * nx + x, rho, Fex, Fey);
-            collide<R>(kp, f, rho, p1[c], Sx, Sy, Fex, Fey, fb, ux, uy);
-            store_node<S>(kp, x, y, fb, rho);
+            external_force<R>(kp, (int64_t)y * nx + col, rho_old, Fex, Fey);
+            collide<R>(kp, f_old, rho_old, psi_m1, Sx, Sy, Fex, Fey, fb, ux, uy);
+            store_node<S>(kp, col, y, fb, rho_old);
         }
-        __syncthreads();
-        // the slot of row rp - 2 is free: stage row rp - 2 + RING into it
-        if (t == 0) {
-            const int rn = rp - 2 + RING;
-            if (rp - 2 >= first && rn <= last) {
-                fence_proxy_async();
-                issue(rn);
-            }
-        }
+        psi_m2 = psi_m1;
+        psi_m1 = psi_new;
+        rho_old = rho_new;
+#pragma unroll
+        for (int i = 0; i < 9; ++i) f_old[i] = f_new[i];
     }
-    if (!ok) {
-        // drain: wait (bounded) for every row still in flight before the CTA exits
-        if (t == 0) {
-            atomicOr(kp.err, DERR_TIMEOUT);
-            for (int r = last - RING + 1; r <= last; ++r)
-                if (r >= first) wait_row(r);
-        }
-        __syncthreads();
-    }
+    if (!ok) atomicOr(kp.err, DERR_TIMEOUT);
+    // release every slot this warp still holds so the producer's bounded waits end early
+    if (!ok && lane == 0)
+        for (int s = 0; s < RING; ++s) mbar_arrive(empty + s);
 }
 
-template <class S, int TX, int RING>
+template <class S, int NW, int RING>
 struct Fused {
-    typedef FusedLayout<S, TX, RING> L;
-    static cudaError_t launch(const KParams &kp, cudaStream_t st)
+    typedef FusedLayout<S, NW, RING> L;
+    template <bool P>
+    static cudaError_t launch_one(const KParams &kp, cudaStream_t st)
     {
         static bool configured = false;
-        const size_t smem = L::bytes(true);
         if (!configured) {
-            cudaError_t e = cudaFuncSetAttribute(k_fused<S, TX, RING>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            cudaError_t e = cudaFuncSetAttribute(k_fused<S, NW, RING, P>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                 (int)L::bytes(true));
             if (e != cudaSuccess) return e;
             configured = true;
         }
         int dev = 0, sms = 148;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        const int strips = (kp.nx + TX - 1) / TX;
+        const int strips = (kp.nx + L::TX - 1) / L::TX;
         int nseg = (16 * sms + strips - 1) / strips;
         const int max_seg = kp.ny / 16 > 0 ? kp.ny / 16 : 1;
         if (nseg > max_seg) nseg = max_seg;
         if (nseg < 1) nseg = 1;
         const int seg_rows = (kp.ny + nseg - 1) / nseg;
         nseg = (kp.ny + seg_rows - 1) / seg_rows;
-        k_fused<S, TX, RING><<<dim3(strips, nseg), TX, L::bytes(kp.per_node_ref != 0), st>>>(kp, seg_rows);
+        k_fused<S, NW, RING, P><<<dim3(strips, nseg), 32 * (NW + 1), L::bytes(kp.per_node_ref != 0), st>>>(kp, seg_rows);
         return cudaGetLastError();
+    }
+    static cudaError_t launch(const KParams &kp, cudaStream_t st)
+    {
+        if (kp.periodic_x && kp.periodic_y) return launch_one<true>(kp, st);
+        return launch_one<false>(kp, st);
     }
 };
 
