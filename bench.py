@@ -319,7 +319,7 @@ def main():
             "scaling": "weak", "vs_baseline": None, "dtype": "f32" if args.precision != "f64" else "f64",
             "data": "synthetic",
             "config": {"workload": "spinodal %dx%d periodic, Carnahan-Starling 0.7Tc, eps 1.895, improved "
-                                   "scheme, tau 0.8, %s population storage" % (n, n, args.precision),
+                                   "scheme, tau %.1f, %s population storage" % (n, n, TAU, args.precision),
                        "nx": n, "ny": n, "storage": args.precision,
                        "l2": "inputs larger than L2 (population buffers %.1f GB each)" % (bpu / 2 * n * n / 1e9),
                        "parallelism": "replicas" if world > 1 else "single"},

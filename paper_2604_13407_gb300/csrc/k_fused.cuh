@@ -87,24 +87,25 @@ struct FusedLayout {
     static size_t bytes(bool ref) { return (size_t)RING * POP_ROW + (ref ? (size_t)RING * REF_ROW : 0) + 2 * RING * 8 + 16; }
 };
 
-// Reads population k of the staged node at (col, row slot) -- col is the staged column.
+// Reads staged populations around one node.  The byte addresses of the three staged
+// rows (y - 1, y, y + 1) at the node's column are formed once per row, so every read is
+// one shared-memory load at a compile-time offset.
 template <class S, int NW, int RING>
 struct RingAt {
     typedef typename Codec<S>::R R;
     typedef FusedLayout<S, NW, RING> L;
     const KParams &kp;
-    const unsigned char *pops;
-    const float *refs;
-    int x_lo, first;
-    // (x, y): unwrapped coordinates within one node of the node being pulled
+    const unsigned char *row[3];  // staged rows y-1, y, y+1, already offset to column cx
+    const float *ref[3];          // same for the reference-density rows (or null)
+    int cx, cy;
+    // (x, y): unwrapped coordinates within one node of (cx, cy)
     __device__ __forceinline__ R operator()(int k, int x, int y) const
     {
-        const int col = x - x_lo;
-        const int slot = (y - first) & (RING - 1);
-        const S *row = reinterpret_cast<const S *>(pops + (size_t)slot * L::POP_ROW) + k * L::W;
+        const int dy = y - cy + 1, dx = x - cx;
+        const S v = reinterpret_cast<const S *>(row[dy])[k * L::W + dx];
         R wref = R(0);
-        if (IsDev<S>::value) wref = w_<R>(k) * (kp.per_node_ref ? R(refs[slot * L::W + col]) : R(kp.rho_ref));
-        return Codec<S>::dec(row[col], wref, R(kp.inv_scale));
+        if (IsDev<S>::value) wref = w_<R>(k) * (kp.per_node_ref ? R(ref[dy][dx]) : R(kp.rho_ref));
+        return Codec<S>::dec(v, wref, R(kp.inv_scale));
     }
 };
 
@@ -205,8 +206,8 @@ __global__ void __launch_bounds__(32 * (NW + 1)) k_fused(KParams kp, int seg_row
     }
 
     // ----------------------------------------------------------- consumer warps
-    const RingAt<S, NW, RING> at{kp, pops, refs, x_lo, first};
     const int col = x0 + 30 * warp - 1 + lane;  // unwrapped column of this lane's node
+    const int scol = col - x_lo;                 // its staged column
     const bool col_out = !PERIODIC && !kp.periodic_x && (col < 0 || col >= nx);
     const bool collides = lane >= 1 && lane <= 30 && col < nx;
     const R psi_s = R(kp.psi_s);
@@ -231,6 +232,13 @@ __global__ void __launch_bounds__(32 * (NW + 1)) k_fused(KParams kp, int seg_row
 #pragma unroll
         for (int i = 0; i < 9; ++i) f_new[i] = R(0);
         if (!col_out && !row_out) {
+            RingAt<S, NW, RING> at{kp, {}, {}, col, rp};
+#pragma unroll
+            for (int d = 0; d < 3; ++d) {
+                const int slot = (rp - 1 + d - first) & (RING - 1);
+                at.row[d] = pops + (size_t)slot * L::POP_ROW + (size_t)scol * sizeof(S);
+                at.ref[d] = refs ? refs + slot * W + scol : nullptr;
+            }
             pull_ring<PERIODIC, R>(kp, col, rp, at, f_new);
             rho_new = density<R>(f_new);
             psi_new = psi_of<R>(kp, rho_new);
