@@ -87,24 +87,60 @@ struct FusedLayout {
     static size_t bytes(bool ref) { return (size_t)RING * POP_ROW + (ref ? (size_t)RING * REF_ROW : 0) + 2 * RING * 8 + 16; }
 };
 
-// Reads staged populations around one node.  The byte addresses of the three staged
-// rows (y - 1, y, y + 1) at the node's column are formed once per row, so every read is
-// one shared-memory load at a compile-time offset.
+// Explicit shared-memory loads (32-bit shared-window addresses).
+template <class S> struct Lds;
+template <> struct Lds<double> {
+    static __device__ __forceinline__ double ld(uint32_t a)
+    {
+        double v;
+        asm volatile("ld.shared.f64 %0, [%1];" : "=d"(v) : "r"(a));
+        return v;
+    }
+};
+template <> struct Lds<float> {
+    static __device__ __forceinline__ float ld(uint32_t a)
+    {
+        float v;
+        asm volatile("ld.shared.f32 %0, [%1];" : "=f"(v) : "r"(a));
+        return v;
+    }
+};
+template <> struct Lds<__half> {
+    static __device__ __forceinline__ __half ld(uint32_t a)
+    {
+        unsigned short v;
+        asm volatile("ld.shared.b16 %0, [%1];" : "=h"(v) : "r"(a));
+        return __ushort_as_half(v);
+    }
+};
+template <> struct Lds<__nv_bfloat16> {
+    static __device__ __forceinline__ __nv_bfloat16 ld(uint32_t a)
+    {
+        unsigned short v;
+        asm volatile("ld.shared.b16 %0, [%1];" : "=h"(v) : "r"(a));
+        return __ushort_as_bfloat16(v);
+    }
+};
+
+// Reads staged populations around one node.  The shared-window addresses of the three
+// staged rows (y - 1, y, y + 1) at the node's column are formed once per row, so every
+// read is one shared load at a compile-time offset from one of three registers.
 template <class S, int NW, int RING>
 struct RingAt {
     typedef typename Codec<S>::R R;
     typedef FusedLayout<S, NW, RING> L;
     const KParams &kp;
-    const unsigned char *row[3];  // staged rows y-1, y, y+1, already offset to column cx
-    const float *ref[3];          // same for the reference-density rows (or null)
+    uint32_t row[3];  // staged rows y-1, y, y+1 at column cx (bytes, shared window)
+    uint32_t ref[3];  // same for the reference-density rows
     int cx, cy;
     // (x, y): unwrapped coordinates within one node of (cx, cy)
     __device__ __forceinline__ R operator()(int k, int x, int y) const
     {
         const int dy = y - cy + 1, dx = x - cx;
-        const S v = reinterpret_cast<const S *>(row[dy])[k * L::W + dx];
+        const S v = Lds<S>::ld(row[dy] + (uint32_t)((k * L::W + dx) * (int)sizeof(S)));
         R wref = R(0);
-        if (IsDev<S>::value) wref = w_<R>(k) * (kp.per_node_ref ? R(ref[dy][dx]) : R(kp.rho_ref));
+        if (IsDev<S>::value)
+            wref = w_<R>(k) * (kp.per_node_ref ? R(Lds<float>::ld(ref[dy] + (uint32_t)(dx * 4))) : R(kp.rho_ref));
         return Codec<S>::dec(v, wref, R(kp.inv_scale));
     }
 };
@@ -208,6 +244,8 @@ __global__ void __launch_bounds__(32 * (NW + 1)) k_fused(KParams kp, int seg_row
     // ----------------------------------------------------------- consumer warps
     const int col = x0 + 30 * warp - 1 + lane;  // unwrapped column of this lane's node
     const int scol = col - x_lo;                 // its staged column
+    const uint32_t pops_s = smem_u32(pops);
+    const uint32_t refs_s = refs ? smem_u32(refs) : 0u;
     const bool col_out = !PERIODIC && !kp.periodic_x && (col < 0 || col >= nx);
     const bool collides = lane >= 1 && lane <= 30 && col < nx;
     const R psi_s = R(kp.psi_s);
@@ -232,12 +270,12 @@ __global__ void __launch_bounds__(32 * (NW + 1)) k_fused(KParams kp, int seg_row
 #pragma unroll
         for (int i = 0; i < 9; ++i) f_new[i] = R(0);
         if (!col_out && !row_out) {
-            RingAt<S, NW, RING> at{kp, {}, {}, col, rp};
+            RingAt<S, NW, RING> at{kp, {0u, 0u, 0u}, {0u, 0u, 0u}, col, rp};
 #pragma unroll
             for (int d = 0; d < 3; ++d) {
-                const int slot = (rp - 1 + d - first) & (RING - 1);
-                at.row[d] = pops + (size_t)slot * L::POP_ROW + (size_t)scol * sizeof(S);
-                at.ref[d] = refs ? refs + slot * W + scol : nullptr;
+                const uint32_t slot = (uint32_t)((rp - 1 + d - first) & (RING - 1));
+                at.row[d] = pops_s + slot * (uint32_t)L::POP_ROW + (uint32_t)(scol * (int)sizeof(S));
+                at.ref[d] = refs_s + slot * (uint32_t)L::REF_ROW + (uint32_t)(scol * 4);
             }
             pull_ring<PERIODIC, R>(kp, col, rp, at, f_new);
             rho_new = density<R>(f_new);
