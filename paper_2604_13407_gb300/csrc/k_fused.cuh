@@ -140,8 +140,8 @@ struct RingAt {
         const S v = Lds<S>::ld(row[dy] + (uint32_t)((k * L::W + dx) * (int)sizeof(S)));
         R wref = R(0);
         if (IsDev<S>::value)
-            wref = w_<R>(k) * (kp.per_node_ref ? R(Lds<float>::ld(ref[dy] + (uint32_t)(dx * 4))) : R(kp.rho_ref));
-        return Codec<S>::dec(v, wref, R(kp.inv_scale));
+            wref = w_<R>(k) * (kp.per_node_ref ? R(Lds<float>::ld(ref[dy] + (uint32_t)(dx * 4))) : cst<R>(kp).rho_ref);
+        return Codec<S>::dec(v, wref, cst<R>(kp).inv_scale);
     }
 };
 
@@ -248,7 +248,7 @@ __global__ void __launch_bounds__(32 * (NW + 1)) k_fused(KParams kp, int seg_row
     const uint32_t refs_s = refs ? smem_u32(refs) : 0u;
     const bool col_out = !PERIODIC && !kp.periodic_x && (col < 0 || col >= nx);
     const bool collides = lane >= 1 && lane <= 30 && col < nx;
-    const R psi_s = R(kp.psi_s);
+    const R psi_s = cst<R>(kp).psi_s;
     R f_old[9], rho_old = R(0), psi_m2 = psi_s, psi_m1 = psi_s;
 #pragma unroll
     for (int i = 0; i < 9; ++i) f_old[i] = R(0);

@@ -25,7 +25,7 @@ struct FieldPsi {
     __device__ __forceinline__ R operator()(int i) const
     {
         int xx = x + ex_(i), yy = y + ey_(i);
-        if (!wrap_xy(kp, xx, yy)) return R(kp.psi_s);
+        if (!wrap_xy(kp, xx, yy)) return cst<R>(kp).psi_s;
         return psi[(int64_t)yy * kp.nx + xx];
     }
 };
@@ -45,7 +45,7 @@ __global__ void __launch_bounds__(kRowThreads) k_psi(KParams kp)
     const int64_t node = (int64_t)y * kp.nx + x;
     R *psi = static_cast<R *>(kp.psi);
     if (node_is_solid(kp, node)) {
-        psi[node] = R(kp.psi_s);
+        psi[node] = cst<R>(kp).psi_s;
         return;
     }
     R f[9];
@@ -149,7 +149,7 @@ __global__ void __launch_bounds__(kRowThreads) k_diag(KParams kp, double *acc, u
         stencil_S<R>(FieldPsi<R>{kp, psi, x, y}, Sx, Sy);
         external_force<R>(kp, node, rho, Fex, Fey);
         collide<R>(kp, f, rho, psi[node], Sx, Sy, Fex, Fey, fb, ux, uy);
-        const R G = R(kp.G);
+        const R G = cst<R>(kp).G;
         const double jx = double(((f[1] - f[3]) + (f[5] - f[6])) + (f[8] - f[7]));
         const double jy = double(((f[2] - f[4]) + (f[5] + f[6])) - (f[7] + f[8]));
         v[0] = double(rho);

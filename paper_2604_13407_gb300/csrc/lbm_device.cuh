@@ -34,6 +34,11 @@ namespace lbm {
 template <class R>
 constexpr bool is_f64() { return std::is_same<R, double>::value; }
 
+// Kernel constants in arithmetic type R.
+template <class R> __device__ __forceinline__ const Consts<R> &cst(const KParams &kp);
+template <> __device__ __forceinline__ const Consts<double> &cst<double>(const KParams &kp) { return kp.cd; }
+template <> __device__ __forceinline__ const Consts<float> &cst<float>(const KParams &kp) { return kp.cf; }
+
 // ------------------------------------------------------------ codecs -------
 // Stored value <-> population.  FP16/BF16 keep (f_i - w_i rho_ref) 2^k, rounded to
 // nearest even; decode multiplies back by 2^-k (exact) and adds w_i rho_ref.
@@ -67,7 +72,7 @@ template <> struct IsDev<__nv_bfloat16> { static constexpr bool value = true; };
 template <class R>
 __device__ __forceinline__ R p_eos(const KParams &kp, R rho)
 {
-    const R a = R(kp.eos_a), b = R(kp.eos_b), RT = R(kp.eos_RT), K = R(kp.eos_K);
+    const R a = cst<R>(kp).eos_a, b = cst<R>(kp).eos_b, RT = cst<R>(kp).eos_RT, K = cst<R>(kp).eos_K;
     if (kp.eos == 0) return K * (rho * RT / (R(1) - b * rho) - a * rho * rho);
     const R eta = b * rho * R(0.25);
     const R om = R(1) - eta;
@@ -79,7 +84,7 @@ template <class R>
 __device__ __forceinline__ R psi_of(const KParams &kp, R rho)
 {
     if constexpr (is_f64<R>()) return f64::psi_of(kp, rho);
-    else return sqrt(R(kp.two_over_G) * (p_eos<R>(kp, rho) - rho / R(3)));
+    else return sqrtf(cst<R>(kp).two_over_G * (p_eos<R>(kp, rho) - rho / R(3)));
 }
 
 // ------------------------------------------------------------ geometry -----
@@ -113,8 +118,8 @@ __device__ __forceinline__ typename Codec<S>::R load_pop(const KParams &kp, int 
     const S *A = static_cast<const S *>(kp.src);
     const int64_t k = (int64_t)y * kp.pitch + x;
     R wref = R(0);
-    if (IsDev<S>::value) wref = w_<R>(i) * (kp.per_node_ref ? R(kp.ref_src[k]) : R(kp.rho_ref));
-    return Codec<S>::dec(A[i * kp.plane + k], wref, R(kp.inv_scale));
+    if (IsDev<S>::value) wref = w_<R>(i) * (kp.per_node_ref ? R(kp.ref_src[k]) : cst<R>(kp).rho_ref);
+    return Codec<S>::dec(A[i * kp.plane + k], wref, cst<R>(kp).inv_scale);
 }
 
 // Link closed by a wall (x - e_i is a wall): the population that left (x, y) toward it
@@ -199,11 +204,11 @@ template <class R>
 __device__ __forceinline__ void external_force(const KParams &kp, int64_t node, R rho, R &Fex, R &Fey)
 {
     if (kp.force_mode == 0) {
-        Fex = R(kp.Fx);
-        Fey = R(kp.Fy);
+        Fex = cst<R>(kp).Fx;
+        Fey = cst<R>(kp).Fy;
     } else if (kp.force_mode == 1) {  // Sec. 3.3: (rho - rho_g) g
-        Fex = (rho - R(kp.rho_g)) * R(kp.Fx);
-        Fey = (rho - R(kp.rho_g)) * R(kp.Fy);
+        Fex = (rho - cst<R>(kp).rho_g) * cst<R>(kp).Fx;
+        Fey = (rho - cst<R>(kp).rho_g) * cst<R>(kp).Fy;
     } else {
         Fex = kp.fext ? R(kp.fext[node]) : R(0);
         Fey = kp.fext ? R(kp.fext[(int64_t)kp.nx * kp.ny + node]) : R(0);
@@ -239,7 +244,7 @@ __device__ __forceinline__ void collide(const KParams &kp, const R (&f)[9], R rh
         f64::collide(kp, f, psi, Sx, Sy, Fex, Fey, fb, ux, uy);
         return;
     }
-    const R G = R(kp.G);
+    const R G = cst<R>(kp).G;
     const R jx = ((f[1] - f[3]) + (f[5] - f[6])) + (f[8] - f[7]);
     const R jy = ((f[2] - f[4]) + (f[5] + f[6])) - (f[7] + f[8]);
     const R Fix = -G * psi * Sx, Fiy = -G * psi * Sy;
@@ -270,24 +275,24 @@ __device__ __forceinline__ void collide(const KParams &kp, const R (&f)[9], R rh
 
     // third-order source with |F_int|^2/(G psi^2) = G |S|^2
     const R Sx2 = Sx * Sx, Sy2 = Sy * Sy;
-    const R Q1 = R(kp.kq1) * (Sx2 + Sy2);
-    const R Q2 = R(kp.q2fac) * Q1;
-    const R Q7 = R(kp.kq7) * (Sx2 - Sy2);
-    const R Q8 = R(kp.kq7) * Sx * Sy;
+    const R Q1 = cst<R>(kp).kq1 * (Sx2 + Sy2);
+    const R Q2 = cst<R>(kp).q2fac * Q1;
+    const R Q7 = cst<R>(kp).kq7 * (Sx2 - Sy2);
+    const R Q8 = cst<R>(kp).kq7 * Sx * Sy;
     R Q4 = R(0), Q6 = R(0);
     if (kp.improved) {
-        Q4 = (R(kp.c1G) * Sx2 - R(kp.c2G) * Sy2) * ux;
-        Q6 = (R(kp.c1G) * Sy2 - R(kp.c2G) * Sx2) * uy;
+        Q4 = (cst<R>(kp).c1G * Sx2 - cst<R>(kp).c2G * Sy2) * ux;
+        Q6 = (cst<R>(kp).c1G * Sy2 - cst<R>(kp).c2G * Sx2) * uy;
     }
 
-    R sp = R(kp.sp), sq = R(kp.sq);
+    R sp = cst<R>(kp).sp, sq = cst<R>(kp).sq;
     if (kp.var_tau) {
-        R wgt = (rho - R(kp.rho_g)) / (R(kp.rho_l) - R(kp.rho_g));
+        R wgt = (rho - cst<R>(kp).rho_g) / (cst<R>(kp).rho_l - cst<R>(kp).rho_g);
         wgt = wgt < R(0) ? R(0) : (wgt > R(1) ? R(1) : wgt);
-        const R nu = R(kp.nu_g) + wgt * (R(kp.nu_l) - R(kp.nu_g));
+        const R nu = cst<R>(kp).nu_g + wgt * (cst<R>(kp).nu_l - cst<R>(kp).nu_g);
         const R tau = R(3) * nu + R(0.5);
         sp = R(1) / tau;
-        sq = R(1) / (R(0.5) + R(kp.Lambda) / (tau - R(0.5)));
+        sq = R(1) / (R(0.5) + cst<R>(kp).Lambda / (tau - R(0.5)));
     }
     const R hsp = R(1) - R(0.5) * sp, hsq = R(1) - R(0.5) * sq;
     // m_bar = (1 - s) m + s m_eq + (1 - s/2) F_m + s Q   (same as Eq. lbe.col)
@@ -356,12 +361,12 @@ __device__ __forceinline__ void store_node(const KParams &kp, int x, int y, cons
     typedef typename Codec<S>::R R;
     S *Bp = static_cast<S *>(kp.dst);
     const int64_t k = (int64_t)y * kp.pitch + x;
-    R ref = R(kp.rho_ref);
+    R ref = cst<R>(kp).rho_ref;
     if (IsDev<S>::value && kp.per_node_ref) {
         ref = rho;
         kp.ref_dst[k] = float(rho);
     }
-    const R scale = R(kp.scale);
+    const R scale = cst<R>(kp).scale;
 #pragma unroll
     for (int i = 0; i < 9; ++i) Bp[i * kp.plane + k] = Codec<S>::enc(fb[i], w_<R>(i) * ref, scale);
 }

@@ -6,8 +6,15 @@
 
 namespace lbm {
 
+// Derived constants in the arithmetic type R of a kernel, computed on the host, so that
+// no kernel converts between double and float per node (GB300's FP64 pipe is narrow).
+template <class R>
+struct Consts {
+    R eos_a, eos_b, eos_RT, eos_K, two_over_G, G, kq1, kq7, c1G, c2G, q2fac, sp, sq, nu_l, nu_g, rho_l, rho_g, Lambda, Fx, Fy, psi_s, rho_ref, scale, inv_scale;
+};
+
 // Everything a kernel needs, passed by value.  Physical constants are kept in double
-// and converted to the arithmetic type of each kernel at its start.
+// (host bookkeeping and the FP64 path) and, for kernels, in cd / cf by arithmetic type.
 struct KParams {
     int nx, ny;
     int64_t pitch;  // elements per row of a population plane (and of the rho_ref plane)
@@ -46,6 +53,8 @@ struct KParams {
     const double *q;       // [8][ny*nx] or null
     const double *fext;    // [2][ny*nx] or null
     int *err;              // device error word (0 = fine)
+    Consts<double> cd;     // constants for FP64 arithmetic
+    Consts<float> cf;      // constants for FP32 arithmetic
 };
 
 // Storage precisions (match lbm_precision)
