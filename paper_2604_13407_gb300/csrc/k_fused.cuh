@@ -161,7 +161,7 @@ __device__ __forceinline__ void pull_ring(const KParams &kp, int cx, int cy, con
     }
 }
 
-template <class S, int NW, int RING, bool PERIODIC>
+template <class S, int NW, int RING, bool PERIODIC, class O>
 __global__ void __launch_bounds__(32 * (NW + 1)) k_fused(KParams kp, int seg_rows)
 {
     typedef typename Codec<S>::R R;
@@ -299,9 +299,20 @@ __global__ void __launch_bounds__(32 * (NW + 1)) k_fused(KParams kp, int seg_row
             };
             R fb[9], Sx, Sy, Fex, Fey, ux, uy;
             stencil_S<R>(ps, Sx, Sy);
-            external_force<R>(kp, (int64_t)y * nx + col, rho_old, Fex, Fey);
-            collide<R>(kp, f_old, rho_old, psi_m1, Sx, Sy, Fex, Fey, fb, ux, uy);
-            store_node<S>(kp, col, y, fb, rho_old);
+            external_force<R, O>(kp, (int64_t)y * nx + col, rho_old, Fex, Fey);
+            collide<R, O>(kp, f_old, rho_old, psi_m1, Sx, Sy, Fex, Fey, fb, ux, uy);
+            // store: one row pointer, planes at a fixed stride
+            S *out = static_cast<S *>(kp.dst) + (int64_t)y * kp.pitch + col;
+            R ref = cst<R>(kp).rho_ref;
+            if (IsDev<S>::value && kp.per_node_ref) {
+                ref = rho_old;
+                kp.ref_dst[(int64_t)y * kp.pitch + col] = float(rho_old);
+            }
+#pragma unroll
+            for (int i = 0; i < 9; ++i) {
+                out[0] = Codec<S>::enc(fb[i], w_<R>(i) * ref, cst<R>(kp).scale);
+                out += kp.plane;
+            }
         }
         psi_m2 = psi_m1;
         psi_m1 = psi_new;
@@ -318,12 +329,12 @@ __global__ void __launch_bounds__(32 * (NW + 1)) k_fused(KParams kp, int seg_row
 template <class S, int NW, int RING>
 struct Fused {
     typedef FusedLayout<S, NW, RING> L;
-    template <bool P>
+    template <bool P, class O>
     static cudaError_t launch_one(const KParams &kp, cudaStream_t st)
     {
         static bool configured = false;
         if (!configured) {
-            cudaError_t e = cudaFuncSetAttribute(k_fused<S, NW, RING, P>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+            cudaError_t e = cudaFuncSetAttribute(k_fused<S, NW, RING, P, O>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                  (int)L::bytes(true));
             if (e != cudaSuccess) return e;
             configured = true;
@@ -338,13 +349,20 @@ struct Fused {
         if (nseg < 1) nseg = 1;
         const int seg_rows = (kp.ny + nseg - 1) / nseg;
         nseg = (kp.ny + seg_rows - 1) / seg_rows;
-        k_fused<S, NW, RING, P><<<dim3(strips, nseg), 32 * (NW + 1), L::bytes(kp.per_node_ref != 0), st>>>(kp, seg_rows);
+        k_fused<S, NW, RING, P, O><<<dim3(strips, nseg), 32 * (NW + 1), L::bytes(kp.per_node_ref != 0), st>>>(kp, seg_rows);
         return cudaGetLastError();
     }
+    // Fully periodic lattices with a constant force and one relaxation time get
+    // instantiations with those options fixed at compile time; everything else reads them
+    // at run time.
     static cudaError_t launch(const KParams &kp, cudaStream_t st)
     {
-        if (kp.periodic_x && kp.periodic_y) return launch_one<true>(kp, st);
-        return launch_one<false>(kp, st);
+        if (kp.periodic_x && kp.periodic_y) {
+            if (kp.force_mode == 0 && !kp.var_tau)
+                return kp.improved ? launch_one<true, Opts<1, 0, 0>>(kp, st) : launch_one<true, Opts<0, 0, 0>>(kp, st);
+            return launch_one<true, RuntimeOpts>(kp, st);
+        }
+        return launch_one<false, RuntimeOpts>(kp, st);
     }
 };
 

@@ -192,6 +192,10 @@ static void fill_constants(lbm_ctx *c)
     LBM_FILL(nu_l) LBM_FILL(nu_g) LBM_FILL(rho_l) LBM_FILL(rho_g) LBM_FILL(Lambda) LBM_FILL(Fx) LBM_FILL(Fy)
     LBM_FILL(psi_s) LBM_FILL(rho_ref) LBM_FILL(scale) LBM_FILL(inv_scale)
 #undef LBM_FILL
+    k.cd.hsp = 1.0 - 0.5 * k.sp;
+    k.cd.hsq = 1.0 - 0.5 * k.sq;
+    k.cf.hsp = 1.0f - 0.5f * (float)k.sp;
+    k.cf.hsq = 1.0f - 0.5f * (float)k.sq;
     k.psi = c->psi;
     k.solid = c->solid;
     k.wall_u = c->wall_u;

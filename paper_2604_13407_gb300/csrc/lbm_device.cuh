@@ -34,6 +34,15 @@ namespace lbm {
 template <class R>
 constexpr bool is_f64() { return std::is_same<R, double>::value; }
 
+// Options a kernel may fix at compile time; -1 means "read from KParams at run time".
+template <int IMPROVED = -1, int VAR_TAU = -1, int FORCE_MODE = -1>
+struct Opts {
+    static __device__ __forceinline__ bool improved(const KParams &kp) { return IMPROVED >= 0 ? IMPROVED != 0 : kp.improved != 0; }
+    static __device__ __forceinline__ bool var_tau(const KParams &kp) { return VAR_TAU >= 0 ? VAR_TAU != 0 : kp.var_tau != 0; }
+    static __device__ __forceinline__ int force_mode(const KParams &kp) { return FORCE_MODE >= 0 ? FORCE_MODE : kp.force_mode; }
+};
+typedef Opts<> RuntimeOpts;
+
 // Kernel constants in arithmetic type R.
 template <class R> __device__ __forceinline__ const Consts<R> &cst(const KParams &kp);
 template <> __device__ __forceinline__ const Consts<double> &cst<double>(const KParams &kp) { return kp.cd; }
@@ -200,13 +209,14 @@ __device__ __forceinline__ R density(const R (&f)[9])
 }
 
 // ------------------------------------------------------------ forces -------
-template <class R>
+template <class R, class O = RuntimeOpts>
 __device__ __forceinline__ void external_force(const KParams &kp, int64_t node, R rho, R &Fex, R &Fey)
 {
-    if (kp.force_mode == 0) {
+    const int mode = O::force_mode(kp);
+    if (mode == 0) {
         Fex = cst<R>(kp).Fx;
         Fey = cst<R>(kp).Fy;
-    } else if (kp.force_mode == 1) {  // Sec. 3.3: (rho - rho_g) g
+    } else if (mode == 1) {  // Sec. 3.3: (rho - rho_g) g
         Fex = (rho - cst<R>(kp).rho_g) * cst<R>(kp).Fx;
         Fey = (rho - cst<R>(kp).rho_g) * cst<R>(kp).Fy;
     } else {
@@ -236,7 +246,7 @@ __device__ __forceinline__ void stencil_S(const Ps &ps, R &Sx, R &Sy)
 // Q_m original or improved (Eqs. qm.improved, qm46.improved); rates s_0 = s_j = 1,
 // s_e = s_eps = s_p = 1/tau, (1/s_q - 1/2)(1/s_p - 1/2) = Lambda (Sec. 3);
 // m_bar = m + F_m - S (m - m_eq + F_m/2) + S Q_m (Eq. lbe.col); f_bar = M^-1 m_bar.
-template <class R>
+template <class R, class O = RuntimeOpts>
 __device__ __forceinline__ void collide(const KParams &kp, const R (&f)[9], R rho, R psi, R Sx, R Sy,
                                         R Fex, R Fey, R (&fb)[9], R &ux, R &uy)
 {
@@ -280,21 +290,23 @@ __device__ __forceinline__ void collide(const KParams &kp, const R (&f)[9], R rh
     const R Q7 = cst<R>(kp).kq7 * (Sx2 - Sy2);
     const R Q8 = cst<R>(kp).kq7 * Sx * Sy;
     R Q4 = R(0), Q6 = R(0);
-    if (kp.improved) {
+    if (O::improved(kp)) {
         Q4 = (cst<R>(kp).c1G * Sx2 - cst<R>(kp).c2G * Sy2) * ux;
         Q6 = (cst<R>(kp).c1G * Sy2 - cst<R>(kp).c2G * Sx2) * uy;
     }
 
     R sp = cst<R>(kp).sp, sq = cst<R>(kp).sq;
-    if (kp.var_tau) {
+    R hsp = cst<R>(kp).hsp, hsq = cst<R>(kp).hsq;
+    if (O::var_tau(kp)) {
         R wgt = (rho - cst<R>(kp).rho_g) / (cst<R>(kp).rho_l - cst<R>(kp).rho_g);
         wgt = wgt < R(0) ? R(0) : (wgt > R(1) ? R(1) : wgt);
         const R nu = cst<R>(kp).nu_g + wgt * (cst<R>(kp).nu_l - cst<R>(kp).nu_g);
         const R tau = R(3) * nu + R(0.5);
         sp = R(1) / tau;
         sq = R(1) / (R(0.5) + cst<R>(kp).Lambda / (tau - R(0.5)));
+        hsp = R(1) - R(0.5) * sp;
+        hsq = R(1) - R(0.5) * sq;
     }
-    const R hsp = R(1) - R(0.5) * sp, hsq = R(1) - R(0.5) * sq;
     // m_bar = (1 - s) m + s m_eq + (1 - s/2) F_m + s Q   (same as Eq. lbe.col)
     const R b1 = m1 - sp * (m1 - meq1) + hsp * Fm1 + sp * Q1;
     const R b2 = m2 - sp * (m2 - meq2) + hsp * Fm2 + sp * Q2;
