@@ -4,7 +4,7 @@
 
 // strip width (consumer warps of 30 columns) and staged-row ring depth of the fused kernel
 #ifndef LBM_FUSED_NW
-#define LBM_FUSED_NW 4
+#define LBM_FUSED_NW 8
 #endif
 #ifndef LBM_FUSED_RING
 #define LBM_FUSED_RING 8

@@ -2,6 +2,14 @@
 #include "k_fused.cuh"
 #include "k_twopass.cuh"
 
+// strip width (consumer warps of 30 columns) and staged-row ring depth of the fused kernel
+#ifndef LBM_FUSED_NW
+#define LBM_FUSED_NW 8
+#endif
+#ifndef LBM_FUSED_RING
+#define LBM_FUSED_RING 8
+#endif
+
 namespace lbm {
 
 Launchers launchers_f64()
@@ -9,13 +17,13 @@ Launchers launchers_f64()
     Launchers L{};
     L.psi_pass = &TwoPass<double>::psi_pass;
     L.collide_pass = &TwoPass<double>::collide_pass;
-    L.fused_pass = &Fused<double, 4, 8>::launch;
+    L.fused_pass = &Fused<double, LBM_FUSED_NW, LBM_FUSED_RING>::launch;
     L.init = &TwoPass<double>::init;
     L.moments = &TwoPass<double>::moments;
     L.diag = &TwoPass<double>::diag;
     L.get_state = &TwoPass<double>::get_state;
     L.set_state = &TwoPass<double>::set_state;
-    L.fused_tile_x = FusedLayout<double, 4, 8>::TX;
+    L.fused_tile_x = FusedLayout<double, LBM_FUSED_NW, LBM_FUSED_RING>::TX;
     L.fused_align = FusedGeom<double>::HX;
     return L;
 }

@@ -218,7 +218,8 @@ static bool fused_possible(const lbm_ctx *c)
     const lbm_params &p = c->p;
     if (c->solid || c->q || c->wall_u) return false;
     if (c->L.fused_align <= 0 || p.nx % c->L.fused_align != 0) return false;
-    if (p.nx < 2 * c->L.fused_tile_x || p.ny < 4) return false;
+    // the wrapped halo segment of the last strip must fit inside the lattice
+    if (p.nx < c->L.fused_tile_x + 16 || p.ny < 4) return false;
     return true;
 }
 
