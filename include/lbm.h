@@ -221,6 +221,30 @@ LBM_API int64_t lbm_step_count(const lbm_ctx *ctx);
 /* Kernel actually used by lbm_step (LBM_KERNEL_TWO_PASS or LBM_KERNEL_FUSED). */
 LBM_API int32_t lbm_kernel_in_use(const lbm_ctx *ctx);
 
+/* Largest lattice (nx * ny) accepted by lbm_step_noalloc_f32. */
+#define LBM_NOALLOC_MAX_NODES (1 << 20)
+
+/* One FP32 time step that allocates nothing (this entry point has no counterpart in the
+ * paper; it serves callers that cannot call cudaMalloc, e.g. while a stream is being
+ * captured into a CUDA graph, or applications that hand all device memory to their own
+ * pool).  Reads the populations of the current state from src and writes the next state
+ * to dst, both caller-owned device memory holding nine planes [9][ny][pitch] of floats
+ * (pitch >= nx elements per row); the step is the two-pass step of lbm_step with
+ * precision LBM_F32 and no geometry arrays (periodic directions or half-way walls at the
+ * domain edges, CONST or BUOYANT force).  Runs on cuda_stream (NULL: the legacy default
+ * stream) and returns without waiting.
+ * Scratch: the pseudopotential field lives in one file-scope device array of
+ * LBM_NOALLOC_MAX_NODES floats (4 MiB) that every device loading the library holds until
+ * exit.  The first call on each device looks up that array's device address with that
+ * device current; make that first call before any stream capture.  All calls on a device
+ * share the array, so calls that overlap on the GPU (other streams, other threads) race:
+ * serialise them.  No call reads scratch left by an earlier one.
+ * Errors (message in lbm_last_error(NULL)): LBM_EINVAL for null or aliasing buffers, a
+ * bad struct_size, pitch < nx, or nx * ny > LBM_NOALLOC_MAX_NODES; LBM_ENOTSUP for a
+ * precision other than LBM_F32 or LBM_FORCE_FIELD; LBM_ECUDA for a failed launch. */
+LBM_API lbm_status lbm_step_noalloc_f32(const lbm_params *p, const float *src, float *dst, int64_t pitch,
+                                        void *cuda_stream);
+
 /* Message of the last failure on ctx (or of the last failed lbm_create when ctx is
  * NULL); never NULL. */
 LBM_API const char *lbm_last_error(const lbm_ctx *ctx);

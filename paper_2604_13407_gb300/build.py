@@ -28,6 +28,7 @@ UNITS = {
     "k_f32.cu": FAST32,
     "k_f16.cu": FAST32,
     "k_bf16.cu": FAST32,
+    "lbm_noalloc.cu": FAST32,
 }
 
 

@@ -667,3 +667,25 @@ ContextView view_of(lbm_ctx *c)
     return v;
 }
 }  // namespace lbm
+
+// ------------------------------------------- helpers for lbm_noalloc.cu ----
+
+namespace lbm {
+// Kernel parameters for a lattice described by *p whose population planes have the given
+// row pitch (elements); no geometry arrays.  Validates *p like lbm_create.
+lbm_status kparams_for(const lbm_params *p, int64_t pitch, KParams *out)
+{
+    lbm_status s = validate(nullptr, *p);
+    if (s != LBM_OK) return s;
+    lbm_ctx tmp;
+    tmp.p = *p;
+    tmp.pitch = pitch;
+    tmp.plane = pitch * p->ny;
+    fill_constants(&tmp);
+    *out = tmp.kp;
+    return LBM_OK;
+}
+
+// Record a message for lbm_last_error(NULL).
+lbm_status set_global_error(lbm_status s, const std::string &msg) { return fail(nullptr, s, msg); }
+}  // namespace lbm

@@ -82,6 +82,7 @@ def load_library(path=None):
         "lbm_step_count": (ctypes.c_int64, [_vp]),
         "lbm_kernel_in_use": (ctypes.c_int32, [_vp]),
         "lbm_last_error": (ctypes.c_char_p, [_vp]),
+        "lbm_step_noalloc_f32": (st, [_P(LbmParams), _vp, _vp, ctypes.c_int64, _vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
