@@ -202,13 +202,24 @@ LBM_API lbm_status lbm_load_state(lbm_ctx *ctx, const void *host_buf, size_t nby
 LBM_API lbm_status lbm_set_param(lbm_ctx *ctx, int32_t which, double value);
 
 /* Adjoint of nsteps forward steps from the current state for the time-averaged
- * objective J = (1/nsteps) sum_{t=1..nsteps} J_t (lbm_objective).  The forward pass
- * stores the populations every checkpoint_every steps, the backward pass recomputes
- * each segment and runs the transposed step.  On return *J holds the objective and
- * grad[0..3] = dJ/d(Fx, Fy, G, T); the state is left at step t0 + nsteps as if
- * lbm_step(nsteps) had run.  FP64 and FP32 storage only (LBM_ENOTSUP otherwise).
+ * objective J = (1/nsteps) sum_{t=1..nsteps} J_t (lbm_objective); the paper has no
+ * adjoint, this differentiates its step (Sec. 2) exactly.  The forward pass advances the
+ * context nsteps steps, storing the populations every checkpoint_every steps and summing
+ * J_t in FP64; the backward pass recomputes each segment from its checkpoint and runs the
+ * transposed step back to the starting state.  On return *J holds the objective,
+ * grad[0..3] = dJ/d(Fx, Fy, G, T) (summed in FP64; dJ/dG is zero up to round-off, since
+ * psi ~ |G|^-1/2 makes the step independent of G), and the state is left at
+ * step t0 + nsteps as if lbm_step(nsteps) had run.
+ * grad and lambda0 both NULL: only the forward pass runs (the objective alone).
  * `lambda0` (may be NULL): receives dJ/d f_bar at the starting state, [9][ny][nx]
- * doubles on the host. */
+ * doubles on the host (zero at solid nodes).
+ * Supported: FP64 and FP32 storage, periodic directions, resting half-way walls (domain
+ * edges and solid nodes), CONST and BUOYANT forces, one or two relaxation times;
+ * LBM_ENOTSUP otherwise.  Device memory (allocated on the first call, kept until
+ * lbm_destroy or a larger call): ceil(nsteps/K) + K - 1 population states, K psi fields
+ * and 15 planes of the arithmetic type, K = min(checkpoint_every, nsteps); LBM_ENOMEM
+ * when it does not fit (lower checkpoint_every).  LBM_EINVAL: nsteps or
+ * checkpoint_every < 1, unknown objective. */
 LBM_API lbm_status lbm_adjoint_step(lbm_ctx *ctx, int64_t nsteps, int32_t checkpoint_every,
                             int32_t objective, double *J, double grad[4], double *lambda0);
 

@@ -1,4 +1,5 @@
 // Kernel instantiations for float population storage.
+#include "k_adjoint.cuh"
 #include "k_fused.cuh"
 #include "k_twopass.cuh"
 
@@ -23,6 +24,10 @@ Launchers launchers_f32()
     L.diag = &TwoPass<float>::diag;
     L.get_state = &TwoPass<float>::get_state;
     L.set_state = &TwoPass<float>::set_state;
+    L.adj_pass1 = &Adjoint<float>::pass1;
+    L.adj_pass2 = &Adjoint<float>::pass2;
+    L.adj_lambda = &Adjoint<float>::lambda;
+    L.objective = &Adjoint<float>::objective;
     L.fused_tile_x = FusedLayout<float, LBM_FUSED_NW, LBM_FUSED_RING>::TX;
     L.fused_align = FusedGeom<float>::HX;
     return L;

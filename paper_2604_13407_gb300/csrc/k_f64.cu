@@ -1,4 +1,5 @@
 // Kernel instantiations for double population storage.
+#include "k_adjoint.cuh"
 #include "k_fused.cuh"
 #include "k_twopass.cuh"
 
@@ -23,6 +24,10 @@ Launchers launchers_f64()
     L.diag = &TwoPass<double>::diag;
     L.get_state = &TwoPass<double>::get_state;
     L.set_state = &TwoPass<double>::set_state;
+    L.adj_pass1 = &Adjoint<double>::pass1;
+    L.adj_pass2 = &Adjoint<double>::pass2;
+    L.adj_lambda = &Adjoint<double>::lambda;
+    L.objective = &Adjoint<double>::objective;
     L.fused_tile_x = FusedLayout<double, LBM_FUSED_NW, LBM_FUSED_RING>::TX;
     L.fused_align = FusedGeom<double>::HX;
     return L;

@@ -1,17 +1,237 @@
-// Checkpointed adjoint of the step (placeholder until the transposed kernels land).
+// Checkpointed adjoint of n steps (host driver of the transposed-step kernels).
+//
+// J = (1/n) sum_{t=1..n} <W, A_t>, with A_t the stored populations after step t and W
+// the weights of the objective.  Reverse-mode differentiation of the time loop:
+//
+//   lambda_n = W/n,  lambda_t = W/n + Step'(A_t)^T lambda_{t+1}  (t = n-1 .. 1),
+//   lambda_0 = Step'(A_0)^T lambda_1,  dJ/dtheta = sum_t (dStep(A_t)/dtheta)^T lambda_{t+1}.
+//
+// Forward sweep: the context advances n steps with its normal kernels, storing A_t every
+// K steps (a checkpoint) and summing <W, A_t> in FP64.  Backward sweep, one segment of K
+// steps at a time from the last: the states of the segment are recomputed from its
+// checkpoint with the two-pass step (whose psi pass leaves the psi field of each state in
+// a buffer of its own), then the transposed step runs from the last state of the segment
+// to the first.  Device memory: ceil(n/K) checkpoints, K - 1 segment states, K psi
+// fields and the adjoint planes; it is kept for the next call with the same sizes.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <string>
+#include <vector>
+
 #include "lbm_adjoint.h"
 
 namespace lbm {
 
 struct AdjointState {
+    void *base = nullptr;
+    size_t bytes = 0;
 };
 
-void adjoint_free(AdjointState *a) { delete a; }
-
-lbm_status adjoint_run(lbm_ctx *, int64_t, int32_t, int32_t, double *, double *, double *, std::string &msg)
+void adjoint_free(AdjointState *a)
 {
-    msg = "adjoint not available in this build";
-    return LBM_ENOTSUP;
+    if (!a) return;
+    if (a->base) cudaFree(a->base);
+    delete a;
+}
+
+namespace {
+
+struct Carver {
+    char *p;
+    size_t used = 0;
+    void *take(size_t bytes)
+    {
+        void *r = p ? p + used : nullptr;
+        used += (bytes + 255) / 256 * 256;
+        return r;
+    }
+};
+
+struct Layout {
+    std::vector<void *> ckpt, seg, psi;
+    void *g[2], *c[2], *dS, *dpsi, *rho;
+    double *acc;
+};
+
+size_t carve(Carver &cv, Layout &L, int64_t nseg, int64_t K, size_t state_bytes, size_t plane_r, size_t psi_bytes)
+{
+    L.ckpt.resize(nseg);
+    L.seg.resize(std::max<int64_t>(K - 1, 1));
+    L.psi.resize(K);
+    for (auto &b : L.ckpt) b = cv.take(state_bytes);
+    for (auto &b : L.seg) b = cv.take(state_bytes);
+    for (auto &b : L.psi) b = cv.take(psi_bytes);
+    for (int s = 0; s < 2; ++s) {
+        L.g[s] = cv.take(9 * plane_r);
+        L.c[s] = cv.take(plane_r);
+    }
+    L.dS = cv.take(2 * plane_r);
+    L.dpsi = cv.take(plane_r);
+    L.rho = cv.take(plane_r);
+    L.acc = static_cast<double *>(cv.take(8 * sizeof(double)));
+    return cv.used;
+}
+
+}  // namespace
+
+#define ACK(call, what)                                                      \
+    do {                                                                     \
+        cudaError_t e_ = (call);                                             \
+        if (e_ != cudaSuccess) {                                             \
+            msg = std::string(what) + ": " + cudaGetErrorString(e_);         \
+            return e_ == cudaErrorMemoryAllocation ? LBM_ENOMEM : LBM_ECUDA; \
+        }                                                                    \
+    } while (0)
+
+lbm_status adjoint_run(lbm_ctx *ctx, int64_t nsteps, int32_t K, int32_t objective, double *J, double *grad,
+                       double *lambda0, std::string &msg)
+{
+    ContextView v = view_of(ctx);
+    const lbm_params &p = *v.p;
+    if (!v.L->adj_pass1) {
+        msg = "the adjoint supports FP64 and FP32 storage only";
+        return LBM_ENOTSUP;
+    }
+    if (v.kp->wall_u || v.kp->q) {
+        msg = "the adjoint supports resting half-way walls only (no wall velocity, no link fractions)";
+        return LBM_ENOTSUP;
+    }
+    if (p.force_mode == LBM_FORCE_FIELD) {
+        msg = "the adjoint supports CONST and BUOYANT forces only";
+        return LBM_ENOTSUP;
+    }
+    if (nsteps < 1 || K < 1 || (objective != LBM_OBJ_WALL_FORCE_Y && objective != LBM_OBJ_MEAN_JX)) {
+        msg = "nsteps and checkpoint_every must be >= 1 and objective one of lbm_objective";
+        return LBM_EINVAL;
+    }
+    if (v.n_fluid < 1) {
+        msg = "no fluid node";
+        return LBM_EINVAL;
+    }
+    cudaStream_t st = v.stream;
+    const int64_t nseg = (nsteps + K - 1) / K;
+    const int64_t Kseg = std::min<int64_t>(K, nsteps);
+    const size_t state_bytes = (size_t)9 * v.plane * v.elem;
+    const size_t real = v.elem;  // arithmetic type = storage type for FP64 and FP32
+    const size_t plane_r = (size_t)v.plane * real;
+    const size_t psi_bytes = (size_t)p.nx * p.ny * real;
+
+    // grad == NULL and lambda0 == NULL: the objective alone (forward sweep only)
+    const bool backward = grad != nullptr || lambda0 != nullptr;
+
+    // device memory, kept across calls
+    Layout L;
+    Carver probe{nullptr};
+    const size_t need = backward ? carve(probe, L, nseg, Kseg, state_bytes, plane_r, psi_bytes)
+                                 : carve(probe, L, 0, 1, 0, 0, 0);
+    AdjointState *&as = *v.adj;
+    if (!as) as = new AdjointState();
+    if (as->bytes < need) {
+        if (as->base) {
+            cudaStreamSynchronize(st);
+            cudaFree(as->base);
+            as->base = nullptr;
+            as->bytes = 0;
+        }
+        cudaError_t e = cudaMalloc(&as->base, need);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            msg = "adjoint: cudaMalloc of " + std::to_string(need >> 20) +
+                  " MiB for checkpoints and segment states failed (lower checkpoint_every)";
+            return LBM_ENOMEM;
+        }
+        as->bytes = need;
+    }
+    Carver cv{static_cast<char *>(as->base)};
+    if (backward) carve(cv, L, nseg, Kseg, state_bytes, plane_r, psi_bytes);
+    else carve(cv, L, 0, 1, 0, 0, 0);
+
+    const double inv_nfluid = 1.0 / double(v.n_fluid);
+    const double w = 1.0 / double(nsteps);
+    ACK(cudaMemsetAsync(L.acc, 0, 8 * sizeof(double), st), "memset");
+
+    // ---- forward sweep: checkpoints and the objective
+    KParams kq = *v.kp;
+    for (int64_t t = 0; t < nsteps; ++t) {
+        if (backward && t % K == 0)
+            ACK(cudaMemcpyAsync(L.ckpt[t / K], v.pops[*v.cur], state_bytes, cudaMemcpyDeviceToDevice, st),
+                "checkpoint copy");
+        lbm_status s = v.run_steps(ctx, 1);
+        if (s != LBM_OK) {
+            msg = "forward step failed";
+            return s;
+        }
+        kq.src = v.pops[*v.cur];
+        ACK(v.L->objective(kq, objective, inv_nfluid, L.acc, st), "objective kernel");
+    }
+
+    if (!backward) {
+        double h0;
+        ACK(cudaMemcpyAsync(&h0, L.acc, sizeof h0, cudaMemcpyDeviceToHost, st), "D2H");
+        ACK(cudaStreamSynchronize(st), "objective");
+        *J = h0 * w;
+        return v.check_error(ctx, msg);
+    }
+
+    // ---- backward sweep
+    AdjArgs aa{};
+    aa.w_scale = w;
+    aa.objective = objective;
+    aa.inv_nfluid = inv_nfluid;
+    aa.grad = L.acc + 1;
+    aa.dS = L.dS;
+    aa.dpsi = L.dpsi;
+    aa.rho = L.rho;
+    int gi = 0;  // buffer holding (g, c) of the step after; none before the first reversal
+    bool have_next = false;
+    for (int64_t s = nseg - 1; s >= 0; --s) {
+        const int64_t t0 = s * K, t1 = std::min<int64_t>((s + 1) * K, nsteps);
+        auto state = [&](int64_t t) -> void * { return t == t0 ? L.ckpt[s] : L.seg[t - t0 - 1]; };
+        KParams kp = *v.kp;
+        for (int64_t t = t0; t < t1; ++t) {
+            kp.src = state(t);
+            kp.psi = L.psi[t - t0];
+            ACK(v.psi_pass(kp, st), "psi kernel");
+            if (t + 1 < t1) {
+                kp.dst = state(t + 1);
+                ACK(v.collide_pass(kp, st), "collide kernel");
+            }
+        }
+        for (int64_t t = t1 - 1; t >= t0; --t) {
+            kp.src = state(t);
+            kp.psi = L.psi[t - t0];
+            aa.g_in = have_next ? L.g[gi] : nullptr;
+            aa.c_in = have_next ? L.c[gi] : nullptr;
+            aa.g_out = L.g[gi ^ 1];
+            aa.c_out = L.c[gi ^ 1];
+            ACK(v.L->adj_pass1(kp, aa, st), "adjoint pass 1");
+            ACK(v.L->adj_pass2(kp, aa, st), "adjoint pass 2");
+            gi ^= 1;
+            have_next = true;
+        }
+    }
+
+    if (lambda0) {
+        const size_t n = (size_t)p.nx * p.ny;
+        double *dl = nullptr;
+        ACK(cudaMalloc((void **)&dl, 9 * n * sizeof(double)), "cudaMalloc(lambda0)");
+        aa.g_in = L.g[gi];
+        aa.c_in = L.c[gi];
+        KParams kp = *v.kp;
+        cudaError_t e = v.L->adj_lambda(kp, aa, dl, st);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(lambda0, dl, 9 * n * sizeof(double), cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        cudaFree(dl);
+        ACK(e, "lambda0");
+    }
+    double h[8];
+    ACK(cudaMemcpyAsync(h, L.acc, sizeof h, cudaMemcpyDeviceToHost, st), "D2H");
+    ACK(cudaStreamSynchronize(st), "adjoint");
+    *J = h[0] * w;
+    if (grad)
+        for (int k = 0; k < 4; ++k) grad[k] = h[1 + k];
+    return v.check_error(ctx, msg);
 }
 
 }  // namespace lbm

@@ -37,6 +37,7 @@ struct lbm_ctx {
     bool initialised = false;
     bool fused_ok = false;
     int64_t steps = 0;
+    int64_t n_fluid = 0;                // nodes that are not solid
     Launchers L{};
     KParams kp{};
     std::string err;
@@ -187,7 +188,7 @@ static void fill_constants(lbm_ctx *c)
     k.inv_scale = std::ldexp(1.0, -p.storage_scale_log2);
     // the same constants in each kernel arithmetic type
 #define LBM_FILL(f) k.cd.f = k.f; k.cf.f = (float)k.f;
-    LBM_FILL(eos_a) LBM_FILL(eos_b) LBM_FILL(eos_RT) LBM_FILL(eos_K) LBM_FILL(two_over_G) LBM_FILL(G)
+    LBM_FILL(eos_a) LBM_FILL(eos_b) LBM_FILL(eos_RT) LBM_FILL(eos_R) LBM_FILL(eos_K) LBM_FILL(two_over_G) LBM_FILL(G)
     LBM_FILL(kq1) LBM_FILL(kq7) LBM_FILL(c1G) LBM_FILL(c2G) LBM_FILL(q2fac) LBM_FILL(sp) LBM_FILL(sq)
     LBM_FILL(nu_l) LBM_FILL(nu_g) LBM_FILL(rho_l) LBM_FILL(rho_g) LBM_FILL(Lambda) LBM_FILL(Fx) LBM_FILL(Fy)
     LBM_FILL(psi_s) LBM_FILL(rho_ref) LBM_FILL(scale) LBM_FILL(inv_scale)
@@ -300,6 +301,7 @@ extern "C" lbm_status lbm_create(const lbm_params *p, void *cuda_stream, lbm_ctx
     cudaMemsetAsync(c->pops[0], 0, pop_bytes, c->stream);
     cudaMemsetAsync(c->pops[1], 0, pop_bytes, c->stream);
     cudaMemsetAsync(c->derr, 0, sizeof(int), c->stream);
+    c->n_fluid = n;
     fill_constants(c);
     choose_kernel(c);
     e = cudaStreamSynchronize(c->stream);
@@ -360,6 +362,9 @@ extern "C" lbm_status lbm_set_geometry(lbm_ctx *c, const uint8_t *solid, const d
     }
     lbm_status s;
     if ((s = upload(c, &c->solid, solid, n, "solid")) != LBM_OK) return s;
+    c->n_fluid = (int64_t)n;
+    if (solid)
+        for (size_t k = 0; k < n; ++k) c->n_fluid -= solid[k] != 0;
     if ((s = upload(c, &c->wall_u, wall_u, 2 * n, "wall_u")) != LBM_OK) return s;
     if ((s = upload(c, &c->q, q, 8 * n, "q")) != LBM_OK) return s;
     if ((s = upload(c, &c->fext, force_field, 2 * n, "force_field")) != LBM_OK) return s;
@@ -614,7 +619,7 @@ extern "C" lbm_status lbm_set_param(lbm_ctx *c, int32_t which, double value)
 extern "C" lbm_status lbm_adjoint_step(lbm_ctx *c, int64_t nsteps, int32_t checkpoint_every, int32_t objective,
                                        double *J, double grad[4], double *lambda0)
 {
-    if (!c || !J || !grad) return LBM_EINVAL;
+    if (!c || !J) return LBM_EINVAL;
     if (!c->initialised) return fail(c, LBM_ESTATE, "fields not initialised");
     std::string msg;
     lbm_status s = adjoint_run(c, nsteps, checkpoint_every, objective, J, grad, lambda0, msg);
@@ -663,6 +668,13 @@ ContextView view_of(lbm_ctx *c)
     v.bind = [](lbm_ctx *cc, int src) { bind_buffers(cc, src); };
     v.psi_pass = c->L.psi_pass;
     v.collide_pass = c->L.collide_pass;
+    v.L = &c->L;
+    v.check_error = [](lbm_ctx *cc, std::string &m) {
+        lbm_status s = check_error_word(cc);
+        if (s != LBM_OK) m = cc->err;
+        return s;
+    };
+    v.n_fluid = c->n_fluid;
     v.ctx = c;
     return v;
 }

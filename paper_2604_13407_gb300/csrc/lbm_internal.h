@@ -10,7 +10,7 @@ namespace lbm {
 // no kernel converts between double and float per node (GB300's FP64 pipe is narrow).
 template <class R>
 struct Consts {
-    R eos_a, eos_b, eos_RT, eos_K, two_over_G, G, kq1, kq7, c1G, c2G, q2fac, sp, sq, nu_l, nu_g, rho_l, rho_g, Lambda, Fx, Fy, psi_s, rho_ref, scale, inv_scale;
+    R eos_a, eos_b, eos_RT, eos_R, eos_K, two_over_G, G, kq1, kq7, c1G, c2G, q2fac, sp, sq, nu_l, nu_g, rho_l, rho_g, Lambda, Fx, Fy, psi_s, rho_ref, scale, inv_scale;
     R hsp, hsq;  // 1 - s_p/2 and 1 - s_q/2 of the constant relaxation rates
 };
 
@@ -58,6 +58,21 @@ struct KParams {
     Consts<float> cf;      // constants for FP32 arithmetic
 };
 
+// Buffers and scalars of one transposed step.  Planes use the population row pitch.
+struct AdjArgs {
+    const void *g_in;   // [9] planes, g of the step after (null: lambda_{t+1} = W_{t+1} only)
+    const void *c_in;   // plane, c of the step after (null with g_in)
+    void *g_out;        // [9] planes
+    void *c_out;        // plane
+    void *dS;           // [2] planes, dJ/dS
+    void *dpsi;         // plane, local part of dJ/dpsi
+    void *rho;          // plane, rho of the pulled populations of A_t
+    double w_scale;     // weight of W in lambda_{t+1} (1/n for J = (1/n) sum_t <W, A_t>)
+    int objective;      // 0: y momentum handed to the walls by the next streaming; 1: mean j_x
+    double inv_nfluid;  // 1 / number of fluid nodes (objective 1)
+    double *grad;       // FP64 accumulators: dJ/dFx, dJ/dFy, dJ/dG, dJ/dT
+};
+
 // Storage precisions (match lbm_precision)
 enum Prec { P_F64 = 0, P_F32 = 1, P_F16 = 2, P_BF16 = 3 };
 
@@ -77,6 +92,11 @@ struct Launchers {
                         cudaStream_t);
     cudaError_t (*get_state)(const KParams &, double *out, cudaStream_t);
     cudaError_t (*set_state)(const KParams &, const double *in, cudaStream_t);
+    // transposed step (FP64 and FP32 storage; null otherwise); AdjArgs in k_adjoint.cuh
+    cudaError_t (*adj_pass1)(const KParams &, const AdjArgs &, cudaStream_t);
+    cudaError_t (*adj_pass2)(const KParams &, const AdjArgs &, cudaStream_t);
+    cudaError_t (*adj_lambda)(const KParams &, const AdjArgs &, double *out, cudaStream_t);
+    cudaError_t (*objective)(const KParams &, int objective, double inv_nfluid, double *acc, cudaStream_t);
     // fused kernel launch constraints
     int fused_tile_x;     // strip width in nodes
     int fused_align;      // nx must be a multiple of this

@@ -247,12 +247,49 @@ class Simulation:
         self._check(self.lib.lbm_load_state(self._h, buf, len(blob)))
 
     # ---- adjoint
-    def adjoint(self, nsteps, checkpoint_every=200, objective=OBJ_WALL_FORCE_Y, want_lambda0=False):
-        """(J, grad[4] = dJ/d(Fx, Fy, G, T), lambda0 or None); advances the state nsteps."""
+    def adjoint(self, nsteps, checkpoint_every=200, objective=OBJ_WALL_FORCE_Y, want_lambda0=False,
+                want_grad=True):
+        """(J, grad[4] = dJ/d(Fx, Fy, G, T) or None, lambda0 or None); advances the state
+        nsteps.  want_grad=False and want_lambda0=False run the forward sweep only."""
         J = ctypes.c_double(0)
-        g = np.zeros(4)
+        g = np.zeros(4) if want_grad else None
         lam = np.zeros((9, self.ny, self.nx)) if want_lambda0 else None
         self._check(self.lib.lbm_adjoint_step(self._h, int(nsteps), int(checkpoint_every), int(objective),
-                                              ctypes.byref(J), g.ctypes.data_as(_dp),
+                                              ctypes.byref(J), g.ctypes.data_as(_dp) if g is not None else None,
                                               lam.ctypes.data if lam is not None else None))
         return J.value, g, lam
+
+    def objective(self, nsteps, objective=OBJ_WALL_FORCE_Y):
+        """J of nsteps steps from the current state (forward sweep only)."""
+        return self.adjoint(nsteps, 1, objective, want_grad=False)[0]
+
+
+_objective_fn = None
+
+
+def time_averaged_objective(sim, theta, snapshot, nsteps, checkpoint_every=200, objective=OBJ_WALL_FORCE_Y):
+    """J(theta) = (1/nsteps) sum_t J_t of nsteps steps from `snapshot` (lbm_save_state bytes),
+    as a torch scalar differentiable in theta = tensor([Fx, Fy, G, T]).  The forward call runs
+    lbm_adjoint_step (the gradient comes from the library's transposed-step kernels); the
+    backward call scales that gradient by the incoming one."""
+    global _objective_fn
+    import torch
+
+    if _objective_fn is None:
+        class _Objective(torch.autograd.Function):
+            @staticmethod
+            def forward(ctx, th, sim_, snap, n, k, obj):
+                for which, value in enumerate(th.detach().cpu().tolist()):
+                    sim_.set_param(which, value)
+                sim_.load_state(snap)
+                J, g, _ = sim_.adjoint(n, k, obj)
+                ctx.save_for_backward(torch.as_tensor(g, dtype=th.dtype, device=th.device))
+                return th.new_tensor(J)
+
+            @staticmethod
+            def backward(ctx, gJ):
+                (g,) = ctx.saved_tensors
+                return gJ * g, None, None, None, None, None
+
+        _objective_fn = _Objective
+    return _objective_fn.apply(theta, sim, snapshot, int(nsteps), int(checkpoint_every), int(objective))

@@ -1,0 +1,189 @@
+"""GPU adjoint (lbm_adjoint_step, the transposed-step kernels) against the FP64 reference
+adjoint of oracle/adjoint_ref.py and against central finite differences.
+
+Tolerances.  FP64: J to 1e-11 relative plus 1e-15 absolute (J is a sum of O(1e-3) terms
+that cancel by two orders of magnitude, or to zero for the y force on the walls of an
+x-periodic channel), dJ/d(Fx, Fy, T) and lambda_0 to 1e-9 of their largest magnitude (the
+GPU sums in another order than autograd).  FP32 arithmetic and storage: J to 1e-4
+relative plus 1e-8 absolute, gradients and lambda_0 to 1e-5 of the largest magnitude (the
+transposed step runs in FP32 about a forward state that carries FP32 rounding; measured
+errors are below 2e-7 and 1e-6).  Finite differences at the full adjoint workload
+(256 x 1024 channel, radius-20 droplet, 4000 steps, checkpoint every 200): central
+differences with a step of 1e-4 relative in FP64; the FP64 and the FP32 adjoint gradients
+within 1e-4 relative of them (measured: 3e-8 and 5e-5)."""
+import numpy as np
+import pytest
+
+from paper_2604_13407_gb300 import inputs as I
+from paper_2604_13407_gb300 import lbm
+from oracle import adjoint_ref as AR
+from tests import gpu_cases as GC
+from tests.setups import cs_case, cs_params
+from tests.test_adjoint_ref import channel_case, droplet_case, initial_state
+
+pytestmark = pytest.mark.gpu
+
+OBJ = {"wall_force_y": lbm.OBJ_WALL_FORCE_Y, "mean_jx": lbm.OBJ_MEAN_JX}
+PARAM_INDEX = (0, 1, 3)  # Fx, Fy, T; index 2 (G) is zero
+
+
+def gpu_sim(p, solid, precision, A0, **kw):
+    sim = lbm.Simulation(GC.gpu_params(p, precision, **kw))
+    if solid is not None:
+        sim.set_geometry(solid)
+    sim.set_state(A0)
+    return sim
+
+
+@pytest.fixture(scope="module")
+def references():
+    out = {}
+    for case in (channel_case, droplet_case):
+        p, rho, solid = case()
+        A0 = initial_state(p, rho, solid)
+        for obj in OBJ:
+            out[(case.__name__, obj)] = (p, solid, A0) + AR.objective_and_grad(p, A0, 12, obj, solid)
+    return out
+
+
+@pytest.mark.parametrize("case", ["channel_case", "droplet_case"])
+@pytest.mark.parametrize("obj", sorted(OBJ))
+@pytest.mark.parametrize("K", [1, 5, 12])
+def test_fp64_adjoint_matches_reference(references, case, obj, K):
+    p, solid, A0, J_ref, g_ref, lam_ref = references[(case, obj)]
+    sim = gpu_sim(p, solid, lbm.F64, A0)
+    J, g, lam = sim.adjoint(12, K, OBJ[obj], want_lambda0=True)
+    assert abs(J - J_ref) <= 1e-11 * abs(J_ref) + 1e-15
+    scale = np.abs(g_ref[list(PARAM_INDEX)]).max()
+    for k in PARAM_INDEX:
+        assert abs(g[k] - g_ref[k]) <= 1e-9 * scale, (k, g[k], g_ref[k])
+    assert abs(g[2]) <= 1e-9 * scale
+    assert np.abs(lam - lam_ref).max() <= 1e-9 * np.abs(lam_ref).max()
+    assert sim.step_count == 12
+
+
+@pytest.mark.parametrize("case", ["channel_case", "droplet_case"])
+@pytest.mark.parametrize("obj", sorted(OBJ))
+def test_fp32_adjoint_matches_reference(references, case, obj):
+    p, solid, A0, J_ref, g_ref, lam_ref = references[(case, obj)]
+    sim = gpu_sim(p, solid, lbm.F32, A0)
+    J, g, lam = sim.adjoint(12, 4, OBJ[obj], want_lambda0=True)
+    assert abs(J - J_ref) <= 1e-4 * abs(J_ref) + 1e-8
+    scale = np.abs(g_ref[list(PARAM_INDEX)]).max()
+    for k in PARAM_INDEX:
+        assert abs(g[k] - g_ref[k]) <= 1e-5 * scale, (k, g[k], g_ref[k])
+    assert abs(g[2]) <= 1e-5 * scale
+    assert np.abs(lam - lam_ref).max() <= 1e-5 * np.abs(lam_ref).max()
+
+
+def test_checkpoint_interval_does_not_change_the_result(references):
+    p, solid, A0, *_ = references[("droplet_case", "wall_force_y")]
+    res = []
+    for K in (1, 3, 12, 100):
+        J, g, lam = gpu_sim(p, solid, lbm.F64, A0).adjoint(12, K, lbm.OBJ_WALL_FORCE_Y, want_lambda0=True)
+        res.append((J, g, lam))
+    for J, g, lam in res[1:]:
+        # J and the gradients are FP64 sums whose block order is not fixed (atomics)
+        assert abs(J - res[0][0]) <= 1e-14 * abs(res[0][0])
+        assert np.abs(g - res[0][1]).max() <= 1e-13 * np.abs(res[0][1]).max()
+        assert np.array_equal(lam, res[0][2])
+
+
+def test_objective_only_and_state_after(references):
+    """grad = lambda0 = NULL runs the forward sweep only; both calls leave the state of
+    lbm_step(n)."""
+    p, solid, A0, *_ = references[("droplet_case", "mean_jx")]
+    a = gpu_sim(p, solid, lbm.F64, A0)
+    J_full, _, _ = a.adjoint(12, 5, lbm.OBJ_MEAN_JX)
+    b = gpu_sim(p, solid, lbm.F64, A0)
+    J_only = b.objective(12, lbm.OBJ_MEAN_JX)
+    c = gpu_sim(p, solid, lbm.F64, A0)
+    c.step(12)
+    assert abs(J_only - J_full) <= 1e-14 * abs(J_full)
+    assert np.array_equal(a.get_state(), c.get_state())
+    assert np.array_equal(b.get_state(), c.get_state())
+
+
+def test_autograd_function_returns_the_adjoint_gradient(references):
+    import torch
+    p, solid, A0, J_ref, g_ref, _ = references[("channel_case", "mean_jx")]
+    sim = gpu_sim(p, solid, lbm.F64, A0)
+    snap = sim.save_state()
+    theta = torch.tensor([p.Fx, p.Fy, p.G, p.T], dtype=torch.float64, requires_grad=True)
+    J = lbm.time_averaged_objective(sim, theta, snap, 12, 4, lbm.OBJ_MEAN_JX)
+    (3.0 * J).backward()
+    assert abs(J.item() - J_ref) <= 1e-11 * abs(J_ref) + 1e-15
+    g = theta.grad.numpy()
+    scale = np.abs(g_ref[list(PARAM_INDEX)]).max()
+    assert np.abs(g[[0, 1, 3]] - 3.0 * g_ref[[0, 1, 3]]).max() <= 3e-9 * scale
+
+
+def test_unsupported_combinations_are_rejected():
+    T, rg, rl = cs_case()
+    p = cs_params(nx=8, ny=8, periodic_x=True, periodic_y=True)
+    sim = lbm.Simulation(GC.gpu_params(p, lbm.F16DEV))
+    sim.init_fields(np.full((8, 8), rl))
+    with pytest.raises(lbm.LbmError) as e:
+        sim.adjoint(2, 1)
+    assert e.value.status == 8
+    sim = lbm.Simulation(GC.gpu_params(p, lbm.F64))
+    sim.init_fields(np.full((8, 8), rl))
+    solid = np.zeros((8, 8), np.uint8)
+    solid[3, 3] = 1
+    wall_u = np.zeros((2, 8, 8))
+    wall_u[0, 3, 3] = 0.01
+    sim.set_geometry(solid, wall_u)
+    with pytest.raises(lbm.LbmError) as e:
+        sim.adjoint(2, 1)
+    assert e.value.status == 8
+    sim.set_geometry(solid)
+    with pytest.raises(lbm.LbmError) as e:
+        sim.adjoint(0, 1)
+    assert e.value.status == 1
+
+
+def droplet_channel_params(precision, **kw):
+    """The adjoint workload: 256 x 1024 channel, walls at x = -1/2 and 255.5, periodic in
+    y, buoyant gravity g = 2e-6 downwards, improved scheme."""
+    op = cs_params(nx=256, ny=1024, periodic_x=False, periodic_y=True, force_mode=1, Fx=0.0, Fy=-2e-6,
+                   scheme=1, tau_l=0.8, tau_g=0.8)
+    return op, GC.gpu_params(op, precision, **kw)
+
+
+def droplet_channel_rho():
+    T, rg, rl = cs_case()
+    cx, cy = I.jittered_centre(4, 128.0, 900.0)
+    return I.droplet(256, 1024, rl, rg, 20.0, cx, cy, periodic_x=False, periodic_y=True)
+
+
+def test_full_workload_gradient_matches_central_differences():
+    n, K = 4000, 200
+    rho0 = droplet_channel_rho()
+    op, p64 = droplet_channel_params(lbm.F64)
+
+    def J_of(which=None, value=None, precision=lbm.F64):
+        _, pp = droplet_channel_params(precision)
+        sim = lbm.Simulation(pp)
+        if which is not None:
+            sim.set_param(which, value)
+        sim.init_fields(rho0)
+        return sim
+
+    sim = J_of()
+    J, g, _ = sim.adjoint(n, K, lbm.OBJ_WALL_FORCE_Y)
+    checks = {}
+    for which, name, base in ((lbm.PARAM_FY, "Fy", op.Fy), (lbm.PARAM_T, "T", op.T)):
+        h = 1e-4 * abs(base)
+        Jp = J_of(which, base + h).objective(n)
+        Jm = J_of(which, base - h).objective(n)
+        fd = (Jp - Jm) / (2 * h)
+        checks[name] = (g[which], fd)
+        assert abs(g[which] - fd) <= 1e-4 * abs(fd), (name, g[which], fd)
+    # G drops out of the step: the normalised sensitivity G dJ/dG vanishes
+    assert abs(g[2] * op.G) <= 1e-8 * abs(g[3] * op.T)
+    # FP32 transposed step on the FP32 forward run
+    sim32 = J_of(precision=lbm.F32)
+    J32, g32, _ = sim32.adjoint(n, K, lbm.OBJ_WALL_FORCE_Y)
+    for which, name in ((lbm.PARAM_FY, "Fy"), (lbm.PARAM_T, "T")):
+        fd = checks[name][1]
+        assert abs(g32[which] - fd) <= 1e-4 * abs(fd), (name, g32[which], fd)
