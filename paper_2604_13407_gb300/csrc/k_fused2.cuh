@@ -1,0 +1,492 @@
+// Fused single-pass step with two nodes per lane and packed FP32 arithmetic, for the
+// storage types whose arithmetic is FP32 (FP32, FP16 and BF16 deviations).
+//
+// Same pipeline as k_fused (k_fused.cuh): one producer warp stages every row of the nine
+// population planes into a shared-memory ring with bulk async copies (full/empty
+// mbarriers, bounded waits); the consumer warps pull, form rho and psi, and one row later
+// collide with the 3 x 3 psi neighbourhood from registers and warp shuffles.  What
+// changes is the work of a lane: it owns two adjacent columns (an even column and the
+// next), so every FP32 addition, multiplication and multiply-add of the step -- moments,
+// EOS, stencil, forces, source term, relaxation, back-transform and storage codec -- is
+// one packed FP32x2 instruction (FADD2 / FMUL2 / FFMA2 of the sm_100 family) for two
+// lattice nodes, the populations of the pair move as 8-byte (FP32) or 4-byte (FP16/BF16)
+// shared loads and global stores, and the psi halo costs two shuffles per row for two
+// nodes.  Reciprocal and square root stay per node.  A warp covers 64 columns: lanes
+// 1..30 update 60 columns, lanes 0 and 31 carry the halo columns.
+//
+// The collision evaluates the same formulas as `collide` (lbm_device.cuh), in packed form
+// and with shared subexpressions, so results agree with the two-pass step to FP32
+// rounding (not bit for bit).  The storage codec rounds exactly as `Codec<>`: the
+// deviation (f - w_i rho_ref) 2^k is formed as one fused multiply-add of f 2^k and
+// -(w_i rho_ref) 2^k, which equals the rounded difference times the power of two.
+#pragma once
+
+#include "k_fused.cuh"
+
+namespace lbm {
+
+// ------------------------------------------------------- packed FP32 pairs --
+struct v2 {
+    float2 v;
+};
+__device__ __forceinline__ v2 V(float a, float b) { return v2{make_float2(a, b)}; }
+__device__ __forceinline__ v2 S2(float a) { return v2{make_float2(a, a)}; }
+__device__ __forceinline__ v2 operator+(v2 a, v2 b) { return v2{__fadd2_rn(a.v, b.v)}; }
+__device__ __forceinline__ v2 operator*(v2 a, v2 b) { return v2{__fmul2_rn(a.v, b.v)}; }
+// a - b rounded once, as one packed multiply-add
+__device__ __forceinline__ v2 operator-(v2 a, v2 b) { return v2{__ffma2_rn(b.v, make_float2(-1.f, -1.f), a.v)}; }
+__device__ __forceinline__ v2 fma2(v2 a, v2 b, v2 c) { return v2{__ffma2_rn(a.v, b.v, c.v)}; }
+__device__ __forceinline__ v2 rcp2(v2 a) { return V(1.0f / a.v.x, 1.0f / a.v.y); }
+__device__ __forceinline__ v2 sqrt2(v2 a) { return V(sqrtf(a.v.x), sqrtf(a.v.y)); }
+
+// ------------------------------------------------------------ staging --------
+template <class S, int NW, int RING>
+struct FusedLayout2 {
+    static constexpr int TX = 60 * NW;                       // output columns per strip
+    static constexpr int HX = FusedGeom<S>::HX;
+    static constexpr int W = TX + 2 * HX;                   // staged columns per row
+    static constexpr int POP_ROW = 9 * W * (int)sizeof(S);  // bytes of one staged row (9 planes)
+    static constexpr int REF_ROW = W * 4;
+    static size_t bytes(bool ref) { return (size_t)RING * POP_ROW + (ref ? (size_t)RING * REF_ROW : 0) + 2 * RING * 8 + 16; }
+};
+
+__device__ __forceinline__ float lds_f32(uint32_t a)
+{
+    float v;
+    asm volatile("ld.shared.f32 %0, [%1];" : "=f"(v) : "r"(a));
+    return v;
+}
+__device__ __forceinline__ v2 lds_v2f32(uint32_t a)
+{
+    float x, y;
+    asm volatile("ld.shared.v2.f32 {%0, %1}, [%2];" : "=f"(x), "=f"(y) : "r"(a));
+    return V(x, y);
+}
+__device__ __forceinline__ uint32_t lds_b32(uint32_t a)
+{
+    uint32_t v;
+    asm volatile("ld.shared.b32 %0, [%1];" : "=r"(v) : "r"(a));
+    return v;
+}
+__device__ __forceinline__ uint32_t lds_b16(uint32_t a)
+{
+    unsigned short v;
+    asm volatile("ld.shared.b16 %0, [%1];" : "=h"(v) : "r"(a));
+    return v;
+}
+
+// Stored pairs <-> FP32 pairs.  `a` is the shared address of the element of column c0;
+// Pair2 loads columns (c0 + off, c0 + off + 1) (off = 0: one aligned load).
+template <class S> struct Pair2;
+template <> struct Pair2<float> {
+    static __device__ __forceinline__ v2 raw(uint32_t a, int off)
+    {
+        if (off == 0) return lds_v2f32(a);
+        return V(lds_f32(a + (uint32_t)(off * 4)), lds_f32(a + (uint32_t)((off + 1) * 4)));
+    }
+    static __device__ __forceinline__ float raw1(uint32_t a) { return lds_f32(a); }
+    static __device__ __forceinline__ void store(float *p, v2 f)
+    {
+        asm volatile("st.global.v2.f32 [%0], {%1, %2};" ::"l"(p), "f"(f.v.x), "f"(f.v.y) : "memory");
+    }
+};
+template <> struct Pair2<__half> {
+    static __device__ __forceinline__ v2 raw(uint32_t a, int off)
+    {
+        uint32_t b = off == 0 ? lds_b32(a) : (lds_b16(a + (uint32_t)(off * 2)) | (lds_b16(a + (uint32_t)((off + 1) * 2)) << 16));
+        __half2 h = *reinterpret_cast<__half2 *>(&b);
+        return v2{__half22float2(h)};
+    }
+    static __device__ __forceinline__ float raw1(uint32_t a) { return __half2float(__ushort_as_half((unsigned short)lds_b16(a))); }
+    static __device__ __forceinline__ void store(__half *p, v2 f)
+    {
+        __half2 h = __float22half2_rn(f.v);
+        asm volatile("st.global.b32 [%0], %1;" ::"l"(p), "r"(*reinterpret_cast<uint32_t *>(&h)) : "memory");
+    }
+};
+template <> struct Pair2<__nv_bfloat16> {
+    static __device__ __forceinline__ v2 raw(uint32_t a, int off)
+    {
+        uint32_t b = off == 0 ? lds_b32(a) : (lds_b16(a + (uint32_t)(off * 2)) | (lds_b16(a + (uint32_t)((off + 1) * 2)) << 16));
+        __nv_bfloat162 h = *reinterpret_cast<__nv_bfloat162 *>(&b);
+        return v2{__bfloat1622float2(h)};
+    }
+    static __device__ __forceinline__ float raw1(uint32_t a) { return __bfloat162float(__ushort_as_bfloat16((unsigned short)lds_b16(a))); }
+    static __device__ __forceinline__ void store(__nv_bfloat16 *p, v2 f)
+    {
+        __nv_bfloat162 h = __float22bfloat162_rn(f.v);
+        asm volatile("st.global.b32 [%0], %1;" ::"l"(p), "r"(*reinterpret_cast<uint32_t *>(&h)) : "memory");
+    }
+};
+
+// ------------------------------------------------------------ physics --------
+// psi = sqrt(2 (p_EOS - rho/3)/G) of two nodes (Sec. 2).
+__device__ __forceinline__ v2 psi_pair(const KParams &kp, v2 rho)
+{
+    const Consts<float> &c = kp.cf;
+    v2 p;
+    if (kp.eos == 0) {
+        const v2 om = fma2(S2(-c.eos_b), rho, S2(1.f));
+        p = S2(c.eos_K) * (rho * S2(c.eos_RT) * rcp2(om) - S2(c.eos_a) * rho * rho);
+    } else {
+        const v2 eta = S2(c.eos_b * 0.25f) * rho;
+        const v2 om = S2(1.f) - eta;
+        const v2 num = fma2(eta, fma2(eta, S2(1.f) - eta, S2(1.f)), S2(1.f));  // 1 + eta + eta^2 - eta^3
+        const v2 den = om * om * om;
+        p = S2(c.eos_K) * (rho * S2(c.eos_RT) * num * rcp2(den) - S2(c.eos_a) * rho * rho);
+    }
+    return sqrt2(S2(c.two_over_G) * fma2(rho, S2(-1.0f / 3.0f), p));
+}
+
+// Stages 5-8 of two nodes (see `collide`): u, m = M f, m_eq, F_m, Q_m, relaxation,
+// f_bar = M^-1 m_bar, with the mass of each node closed through f_bar_0.
+template <class O>
+__device__ __forceinline__ void collide_pair(const KParams &kp, const v2 (&f)[9], v2 rho, v2 psi, v2 Sx, v2 Sy,
+                                             v2 Fex, v2 Fey, v2 (&fb)[9])
+{
+    const Consts<float> &c = kp.cf;
+    const v2 a13 = f[1] - f[3], c24 = f[2] - f[4];
+    const v2 bx = (f[5] - f[6]) + (f[8] - f[7]);
+    const v2 by = (f[5] + f[6]) - (f[7] + f[8]);
+    const v2 jx = a13 + bx, jy = c24 + by;
+    const v2 nGpsi = S2(-c.G) * psi;
+    const v2 Fix = nGpsi * Sx, Fiy = nGpsi * Sy;
+    const v2 Fx = Fix + Fex, Fy = Fiy + Fey;
+    const v2 inv = rcp2(rho);
+    const v2 ux = fma2(S2(0.5f), Fx, jx) * inv;
+    const v2 uy = fma2(S2(0.5f), Fy, jy) * inv;
+
+    // non-conserved moments of M f
+    const v2 p13 = f[1] + f[3], p24 = f[2] + f[4], p57 = f[5] + f[7], p68 = f[6] + f[8];
+    const v2 s14 = p13 + p24, s58 = p57 + p68;
+    const v2 m1 = fma2(S2(-4.f), f[0], fma2(S2(-1.f), s14, s58 + s58));
+    const v2 m2 = fma2(S2(4.f), f[0], fma2(S2(-2.f), s14, s58));
+    const v2 m4 = fma2(S2(-2.f), a13, bx);
+    const v2 m6 = fma2(S2(-2.f), c24, by);
+    const v2 m7 = p13 - p24;
+    const v2 m8 = p57 - p68;
+
+    // equilibrium and forcing moments
+    const v2 rux = rho * ux, ruy = rho * uy;
+    const v2 u2 = fma2(ux, ux, uy * uy);
+    const v2 meq1 = rho * fma2(S2(3.f), u2, S2(-2.f));
+    const v2 meq2 = rho * fma2(S2(-3.f), u2, S2(1.f));
+    const v2 meq7 = fma2(rux, ux, S2(-1.f) * (ruy * uy));
+    const v2 meq8 = rux * uy;
+    const v2 Fu = fma2(Fx, ux, Fy * uy);
+    const v2 Fm7 = S2(2.f) * fma2(Fx, ux, S2(-1.f) * (Fy * uy));
+    const v2 Fm8 = fma2(Fx, uy, Fy * ux);
+
+    // third-order source, |F_int|^2/(G psi^2) = G |S|^2
+    const v2 Sx2 = Sx * Sx, Sy2 = Sy * Sy;
+    const v2 Q1 = S2(c.kq1) * (Sx2 + Sy2);
+    const v2 Q2 = S2(c.q2fac) * Q1;
+    const v2 Q7 = S2(c.kq7) * (Sx2 - Sy2);
+    const v2 Q8 = S2(c.kq7) * Sx * Sy;
+    v2 Q4 = S2(0.f), Q6 = S2(0.f);
+    if (O::improved(kp)) {
+        Q4 = fma2(S2(c.c1G), Sx2, S2(-c.c2G) * Sy2) * ux;
+        Q6 = fma2(S2(c.c1G), Sy2, S2(-c.c2G) * Sx2) * uy;
+    }
+
+    v2 sp = S2(c.sp), sq = S2(c.sq), hsp = S2(c.hsp), hsq = S2(c.hsq);
+    if (O::var_tau(kp)) {
+        v2 w = (rho - S2(c.rho_g)) * S2(1.0f / (c.rho_l - c.rho_g));
+        w = V(fminf(fmaxf(w.v.x, 0.f), 1.f), fminf(fmaxf(w.v.y, 0.f), 1.f));
+        const v2 tau = fma2(S2(3.f), fma2(w, S2(c.nu_l - c.nu_g), S2(c.nu_g)), S2(0.5f));
+        sp = rcp2(tau);
+        sq = rcp2(fma2(S2(c.Lambda), rcp2(tau - S2(0.5f)), S2(0.5f)));
+        hsp = fma2(S2(-0.5f), sp, S2(1.f));
+        hsq = fma2(S2(-0.5f), sq, S2(1.f));
+    }
+    // m_bar = m + s (m_eq - m + Q) + (1 - s/2) F_m   (Eq. lbe.col)
+    const v2 b1 = fma2(sp, (meq1 - m1) + Q1, fma2(S2(6.f) * hsp, Fu, m1));
+    const v2 b2 = fma2(sp, (meq2 - m2) + Q2, fma2(S2(-6.f) * hsp, Fu, m2));
+    const v2 b4 = fma2(sq, (S2(-1.f) * rux - m4) + Q4, fma2(S2(-1.f) * hsq, Fx, m4));
+    const v2 b6 = fma2(sq, (S2(-1.f) * ruy - m6) + Q6, fma2(S2(-1.f) * hsq, Fy, m6));
+    const v2 b7 = fma2(sp, (meq7 - m7) + Q7, fma2(hsp, Fm7, m7));
+    const v2 b8 = fma2(sp, (meq8 - m8) + Q8, fma2(hsp, Fm8, m8));
+    // s_j = 1: m_bar_j = j + F
+
+    // f_bar = M^T diag(1/9, 1/36, 1/36, 1/6, 1/12, 1/6, 1/12, 1/4, 1/4) m_bar
+    const v2 A0 = rho * S2(1.0f / 9.0f), B = b1 * S2(1.0f / 36.0f), C = b2 * S2(1.0f / 36.0f);
+    const v2 D = (jx + Fx) * S2(1.0f / 6.0f), E = b4 * S2(1.0f / 12.0f);
+    const v2 Gy = (jy + Fy) * S2(1.0f / 6.0f), H = b6 * S2(1.0f / 12.0f);
+    const v2 P = b7 * S2(0.25f), Qp = b8 * S2(0.25f);
+    const v2 ax = fma2(S2(-2.f), C, A0 - B);
+    const v2 dg = fma2(S2(2.f), B, A0 + C);
+    const v2 DE = fma2(S2(-2.f), E, D), GH = fma2(S2(-2.f), H, Gy);
+    const v2 DEp = D + E, GHp = Gy + H;
+    fb[1] = (ax + DE) + P;
+    fb[2] = (ax + GH) - P;
+    fb[3] = (ax - DE) + P;
+    fb[4] = (ax - GH) - P;
+    fb[5] = (dg + DEp) + (GHp + Qp);
+    fb[6] = (dg - DEp) + (GHp - Qp);
+    fb[7] = (dg - DEp) - (GHp - Qp);
+    fb[8] = (dg + DEp) - (GHp + Qp);
+    fb[0] = rho - (((fb[1] + fb[2]) + (fb[3] + fb[4])) + ((fb[5] + fb[6]) + (fb[7] + fb[8])));
+}
+
+template <class O>
+__device__ __forceinline__ void external_force_pair(const KParams &kp, int64_t node, v2 rho, v2 &Fex, v2 &Fey)
+{
+    const int mode = O::force_mode(kp);
+    if (mode == 0) {
+        Fex = S2(kp.cf.Fx);
+        Fey = S2(kp.cf.Fy);
+    } else if (mode == 1) {  // Sec. 3.3: (rho - rho_g) g
+        const v2 d = rho - S2(kp.cf.rho_g);
+        Fex = d * S2(kp.cf.Fx);
+        Fey = d * S2(kp.cf.Fy);
+    } else {
+        const int64_t n = (int64_t)kp.nx * kp.ny;
+        Fex = kp.fext ? V(float(kp.fext[node]), float(kp.fext[node + 1])) : S2(0.f);
+        Fey = kp.fext ? V(float(kp.fext[n + node]), float(kp.fext[n + node + 1])) : S2(0.f);
+    }
+}
+
+// ------------------------------------------------------------- kernel --------
+template <class S, int NW, int RING, bool PERIODIC, class O>
+__global__ void __launch_bounds__(32 * (NW + 1)) k_fused2(KParams kp, int seg_rows)
+{
+    typedef FusedLayout2<S, NW, RING> L;
+    constexpr int TX = L::TX, HX = L::HX, W = L::W;
+    constexpr uint32_t ES = sizeof(S);
+    extern __shared__ __align__(128) unsigned char smem[];
+    unsigned char *pops = smem;
+    float *refs = kp.per_node_ref ? reinterpret_cast<float *>(smem + (size_t)RING * L::POP_ROW) : nullptr;
+    uint64_t *full = reinterpret_cast<uint64_t *>(smem + (size_t)RING * L::POP_ROW +
+                                                  (kp.per_node_ref ? (size_t)RING * L::REF_ROW : 0));
+    uint64_t *empty = full + RING;
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int nx = kp.nx, ny = kp.ny;
+    const int x0 = blockIdx.x * TX;
+    const int yb = blockIdx.y * seg_rows;
+    const int ye = min(yb + seg_rows, ny);
+    const int first = yb - 2, last = ye + 1;  // staged rows
+    const int x_lo = x0 - HX;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < RING; ++s) {
+            mbar_init(full + s, 1);
+            mbar_init(empty + s, NW);
+        }
+        fence_mbar_init();
+        fence_proxy_async();
+    }
+    __syncthreads();
+
+    if (warp == NW) {
+        // ------------------------------------------------------ producer warp
+        if (lane != 0) return;
+        const S *A = static_cast<const S *>(kp.src);
+        int r = first;
+        for (; r <= last; ++r) {
+            const int slot = (r - first) & (RING - 1);
+            const int use = (r - first) / RING;
+            if (use > 0 && !mbar_wait_bounded(empty + slot, (uint32_t)((use - 1) & 1))) {
+                atomicOr(kp.err, DERR_TIMEOUT);
+                break;
+            }
+            uint64_t *bar = full + slot;
+            int gy = r;
+            if (gy < 0 || gy >= ny) {
+                if (!kp.periodic_y) {
+                    mbar_arrive(bar);
+                    continue;
+                }
+                gy = ((gy % ny) + ny) % ny;
+            }
+            int sx[3], dx[3], cnt[3], nseg = 0;
+            const int lo = x_lo, hi = x0 + TX + HX;
+            const int m0 = lo < 0 ? 0 : lo, m1 = hi > nx ? nx : hi;
+            sx[nseg] = m0, dx[nseg] = m0 - lo, cnt[nseg] = m1 - m0, ++nseg;
+            if (lo < 0 && kp.periodic_x) sx[nseg] = nx + lo, dx[nseg] = 0, cnt[nseg] = -lo, ++nseg;
+            if (hi > nx && kp.periodic_x) sx[nseg] = 0, dx[nseg] = nx - lo, cnt[nseg] = hi - nx, ++nseg;
+            uint32_t cols = 0;
+            for (int q = 0; q < nseg; ++q) cols += cnt[q];
+            fence_proxy_async();
+            mbar_expect_tx(bar, cols * (9u * ES + (refs ? 4u : 0u)));
+            unsigned char *prow = pops + (size_t)slot * L::POP_ROW;
+            for (int i = 0; i < 9; ++i) {
+                const S *src = A + i * kp.plane + (int64_t)gy * kp.pitch;
+                S *dst = reinterpret_cast<S *>(prow) + i * W;
+                for (int q = 0; q < nseg; ++q) bulk_g2s(dst + dx[q], src + sx[q], cnt[q] * ES, bar);
+            }
+            if (refs) {
+                const float *src = kp.ref_src + (int64_t)gy * kp.pitch;
+                float *dst = refs + slot * W;
+                for (int q = 0; q < nseg; ++q) bulk_g2s(dst + dx[q], src + sx[q], cnt[q] * 4u, bar);
+            }
+        }
+        // drain: every issued row must have landed before the CTA may exit
+        for (int q = max(first, r - RING); q < r && q <= last; ++q)
+            mbar_wait_bounded(full + ((q - first) & (RING - 1)), (uint32_t)(((q - first) / RING) & 1));
+        return;
+    }
+
+    // ----------------------------------------------------------- consumer warps
+    const int c0 = x0 + 60 * warp - 2 + 2 * lane;  // unwrapped column of this lane's first node (even)
+    const int scol = c0 - x_lo;                     // its staged column (even)
+    const uint32_t pops_s = smem_u32(pops);
+    const uint32_t refs_s = refs ? smem_u32(refs) : 0u;
+    const bool col_out = !PERIODIC && !kp.periodic_x && (c0 < 0 || c0 >= nx);  // both nodes (nx is even)
+    const bool collides = lane >= 1 && lane <= 30 && c0 < nx;
+    const bool dev = IsDev<S>::value;
+    const float inv_scale = kp.cf.inv_scale, scale = kp.cf.scale, rho_ref = kp.cf.rho_ref;
+    const v2 psi_s = S2(kp.cf.psi_s);
+    v2 f_old[9], rho_old = S2(0.f), psi_m2 = psi_s, psi_m1 = psi_s;
+#pragma unroll
+    for (int i = 0; i < 9; ++i) f_old[i] = S2(0.f);
+    auto wait_full = [&](int r) -> bool {
+        const bool got = mbar_wait_bounded(full + ((r - first) & (RING - 1)), (uint32_t)(((r - first) / RING) & 1));
+        return __all_sync(0xffffffffu, got);
+    };
+    bool ok = wait_full(first) && wait_full(first + 1);
+    for (int rp = yb - 1; rp <= ye && ok; ++rp) {
+        if (!wait_full(rp + 1)) {
+            ok = false;
+            break;
+        }
+        const bool row_out = !PERIODIC && !kp.periodic_y && (rp < 0 || rp >= ny);
+        v2 f_new[9], rho_new = S2(0.f), psi_new = psi_s;
+#pragma unroll
+        for (int i = 0; i < 9; ++i) f_new[i] = S2(0.f);
+        if (!col_out && !row_out) {
+            uint32_t row[3], ref[3];
+#pragma unroll
+            for (int d = 0; d < 3; ++d) {
+                const uint32_t slot = (uint32_t)((rp - 1 + d - first) & (RING - 1));
+                row[d] = pops_s + slot * (uint32_t)L::POP_ROW + (uint32_t)scol * ES;
+                ref[d] = refs_s + slot * (uint32_t)L::REF_ROW + (uint32_t)scol * 4u;
+            }
+            // pull, Eq. (lbe.str): population i of the pair comes from columns c0 - e_ix (+1)
+            // of row rp - e_iy
+#pragma unroll
+            for (int i = 0; i < 9; ++i) {
+                const int d = 1 - ey_(i), off = -ex_(i);
+                v2 v = Pair2<S>::raw(row[d] + (uint32_t)(i * W) * ES, off);
+                if (dev) {
+                    const v2 wref = kp.per_node_ref
+                                        ? S2(w_<float>(i)) * (off == 0 ? lds_v2f32(ref[d]) :
+                                                              V(lds_f32(ref[d] + (uint32_t)(off * 4)), lds_f32(ref[d] + (uint32_t)((off + 1) * 4))))
+                                        : S2(w_<float>(i) * rho_ref);
+                    v = fma2(v, S2(inv_scale), wref);
+                }
+                f_new[i] = v;
+            }
+            if (!PERIODIC) {
+                // links whose source lies beyond a non-periodic edge: half-way bounce-back
+#pragma unroll
+                for (int i = 1; i < 9; ++i) {
+                    const int ys = rp - ey_(i);
+                    const bool yw = !kp.periodic_y && (ys < 0 || ys >= ny);
+                    const bool w0 = yw || (!kp.periodic_x && (c0 - ex_(i) < 0 || c0 - ex_(i) >= nx));
+                    const bool w1 = yw || (!kp.periodic_x && (c0 + 1 - ex_(i) < 0 || c0 + 1 - ex_(i) >= nx));
+                    if (w0 || w1) {
+                        const int o = opp_(i);
+                        const uint32_t a = row[1] + (uint32_t)(o * W) * ES;
+                        float r0 = Pair2<S>::raw1(a), r1 = Pair2<S>::raw1(a + ES);
+                        if (dev) {
+                            const float rf0 = kp.per_node_ref ? lds_f32(ref[1]) : rho_ref;
+                            const float rf1 = kp.per_node_ref ? lds_f32(ref[1] + 4u) : rho_ref;
+                            r0 = r0 * inv_scale + w_<float>(o) * rf0;
+                            r1 = r1 * inv_scale + w_<float>(o) * rf1;
+                        }
+                        if (w0) f_new[i].v.x = r0 + 0.f;
+                        if (w1) f_new[i].v.y = r1 + 0.f;
+                    }
+                }
+            }
+            rho_new = (((f_new[0] + f_new[1]) + (f_new[2] + f_new[3])) + ((f_new[4] + f_new[5]) + (f_new[6] + f_new[7]))) + f_new[8];
+            psi_new = psi_pair(kp, rho_new);
+        }
+        __syncwarp();
+        // row rp - 1 is not needed any more by this warp
+        if (lane == 0 && rp - 1 >= first) mbar_arrive(empty + ((rp - 1 - first) & (RING - 1)));
+        // psi of the columns left of the pair and right of it, from the adjacent lanes
+        const float am = __shfl_up_sync(0xffffffffu, psi_m2.v.y, 1), bm = __shfl_down_sync(0xffffffffu, psi_m2.v.x, 1);
+        const float a0 = __shfl_up_sync(0xffffffffu, psi_m1.v.y, 1), b0 = __shfl_down_sync(0xffffffffu, psi_m1.v.x, 1);
+        const float ap = __shfl_up_sync(0xffffffffu, psi_new.v.y, 1), bp = __shfl_down_sync(0xffffffffu, psi_new.v.x, 1);
+        const int y = rp - 1;
+        if (collides && y >= yb) {
+            // rows y-1 (m), y (0), y+1 (p); left (L), centre, right (R) columns of each node
+            const v2 Lm = V(am, psi_m2.v.x), Rm = V(psi_m2.v.y, bm);
+            const v2 L0 = V(a0, psi_m1.v.x), R0 = V(psi_m1.v.y, b0);
+            const v2 Lp = V(ap, psi_new.v.x), Rp = V(psi_new.v.y, bp);
+            // S = sum w psi(x + e) e, w = 1/3 (axes), 1/12 (diagonals), Eq. (fint)
+            const v2 dd = Rp - Lm;
+            const v2 Sx = fma2(S2(1.0f / 3.0f), R0 - L0, S2(1.0f / 12.0f) * (dd + (Rm - Lp)));
+            const v2 Sy = fma2(S2(1.0f / 3.0f), psi_new - psi_m2, S2(1.0f / 12.0f) * (dd + (Lp - Rm)));
+            v2 fb[9], Fex, Fey;
+            external_force_pair<O>(kp, (int64_t)y * nx + c0, rho_old, Fex, Fey);
+            collide_pair<O>(kp, f_old, rho_old, psi_m1, Sx, Sy, Fex, Fey, fb);
+            S *out = static_cast<S *>(kp.dst) + (int64_t)y * kp.pitch + c0;
+            if (!dev) {
+#pragma unroll
+                for (int i = 0; i < 9; ++i) Pair2<S>::store(out + i * kp.plane, fb[i]);
+            } else {
+                v2 ref2 = S2(rho_ref);
+                if (kp.per_node_ref) {
+                    ref2 = rho_old;
+                    Pair2<float>::store(kp.ref_dst + (int64_t)y * kp.pitch + c0, rho_old);
+                }
+#pragma unroll
+                for (int i = 0; i < 9; ++i) {
+                    // (f - w_i ref) 2^k as one rounding: f 2^k - (w_i ref) 2^k
+                    const v2 nwref = S2(-scale) * (S2(w_<float>(i)) * ref2);
+                    Pair2<S>::store(out + i * kp.plane, fma2(fb[i], S2(scale), nwref));
+                }
+            }
+        }
+        psi_m2 = psi_m1;
+        psi_m1 = psi_new;
+        rho_old = rho_new;
+#pragma unroll
+        for (int i = 0; i < 9; ++i) f_old[i] = f_new[i];
+    }
+    if (!ok) atomicOr(kp.err, DERR_TIMEOUT);
+    if (!ok && lane == 0)
+        for (int s = 0; s < RING; ++s) mbar_arrive(empty + s);
+}
+
+template <class S, int NW, int RING>
+struct Fused2 {
+    typedef FusedLayout2<S, NW, RING> L;
+    template <bool P, class O>
+    static cudaError_t launch_one(const KParams &kp, cudaStream_t st)
+    {
+        static bool configured = false;
+        if (!configured) {
+            cudaError_t e = cudaFuncSetAttribute(k_fused2<S, NW, RING, P, O>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                 (int)L::bytes(true));
+            if (e != cudaSuccess) return e;
+            configured = true;
+        }
+        int dev = 0, sms = 148;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        const int strips = (kp.nx + L::TX - 1) / L::TX;
+        int nseg = (16 * sms + strips - 1) / strips;
+        const int max_seg = kp.ny / 16 > 0 ? kp.ny / 16 : 1;
+        if (nseg > max_seg) nseg = max_seg;
+        if (nseg < 1) nseg = 1;
+        const int seg_rows = (kp.ny + nseg - 1) / nseg;
+        nseg = (kp.ny + seg_rows - 1) / seg_rows;
+        k_fused2<S, NW, RING, P, O><<<dim3(strips, nseg), 32 * (NW + 1), L::bytes(kp.per_node_ref != 0), st>>>(kp, seg_rows);
+        return cudaGetLastError();
+    }
+    static cudaError_t launch(const KParams &kp, cudaStream_t st)
+    {
+        if (kp.periodic_x && kp.periodic_y) {
+            if (kp.force_mode == 0 && !kp.var_tau)
+                return kp.improved ? launch_one<true, Opts<1, 0, 0>>(kp, st) : launch_one<true, Opts<0, 0, 0>>(kp, st);
+            return launch_one<true, RuntimeOpts>(kp, st);
+        }
+        return launch_one<false, RuntimeOpts>(kp, st);
+    }
+};
+
+}  // namespace lbm
