@@ -106,7 +106,8 @@ typedef struct lbm_params {
     int32_t per_node_ref;           /* FP16/BF16 storage: 1 = deviations from w_i rho(x) of
                                        the writing node (extra FP32 plane), 0 = from
                                        w_i rho_ref */
-    int32_t storage_scale_log2;     /* FP16/BF16 storage of (f_i - w_i rho_ref) 2^k */
+    int32_t storage_scale_log2;     /* FP16/BF16 storage of (f_i - w_i rho_ref) 2^k; k in
+                                       [-30, 30], for FP16 in [-15, 24] */
     double a, b, R, T, K_eos;       /* EOS coefficients */
     double G;                       /* interaction strength, < 0 (Sec. 2) */
     double k1, k2;                  /* source coefficients, epsilon = -8 (k1 + k2) */

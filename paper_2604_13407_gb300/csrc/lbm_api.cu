@@ -124,6 +124,8 @@ static lbm_status validate(lbm_ctx *c, const lbm_params &p)
     if (!(p.Lambda > 0.0)) return fail(c, LBM_EINVAL, "Lambda must be > 0");
     if (p.tau_l != p.tau_g && !(p.rho_l > p.rho_g)) return fail(c, LBM_EINVAL, "rho_l must exceed rho_g when tau_l != tau_g");
     if (p.storage_scale_log2 < -30 || p.storage_scale_log2 > 30) return fail(c, LBM_EINVAL, "storage_scale_log2 out of range");
+    if (p.precision == LBM_F16DEV && (p.storage_scale_log2 < -15 || p.storage_scale_log2 > 24))
+        return fail(c, LBM_EINVAL, "FP16 storage needs storage_scale_log2 in [-15, 24] (2^-k must be an FP16 value)");
     double rmax = p.rho_max > 0 ? p.rho_max : 1.25 * std::fmax(std::fmax(p.rho_l, p.rho_g), p.rho_s);
     if (!(rmax > 0)) return fail(c, LBM_EINVAL, "rho_max must be > 0");
     for (int k = 1; k <= 4096; ++k) {
@@ -197,6 +199,35 @@ static void fill_constants(lbm_ctx *c)
     k.cd.hsq = 1.0 - 0.5 * k.sq;
     k.cf.hsp = 1.0f - 0.5f * (float)k.sp;
     k.cf.hsq = 1.0f - 0.5f * (float)k.sq;
+    {
+        auto P = [](float v) { return make_float2(v, v); };
+        PairConsts &q = k.c2;
+        const Consts<float> &f = k.cf;
+        q.one = P(1.f), q.m_one = P(-1.f), q.half = P(0.5f), q.m_half = P(-0.5f), q.two = P(2.f), q.m_two = P(-2.f);
+        q.three = P(3.f), q.m_three = P(-3.f), q.four = P(4.f), q.m_four = P(-4.f), q.six = P(6.f), q.m_six = P(-6.f);
+        q.third = P(1.0f / 3.0f), q.m_third = P(-1.0f / 3.0f), q.twelfth = P(1.0f / 12.0f), q.ninth = P(1.0f / 9.0f);
+        q.w36 = P(1.0f / 36.0f), q.sixth = P(1.0f / 6.0f), q.quarter = P(0.25f);
+        q.m_G = P(-f.G), q.kq1 = P(f.kq1), q.q2fac = P(f.q2fac), q.kq7 = P(f.kq7), q.c1G = P(f.c1G), q.m_c2G = P(-f.c2G);
+        q.sp = P(f.sp), q.sq = P(f.sq), q.hsp = P(f.hsp), q.hsq = P(f.hsq), q.six_hsp = P(6.f * f.hsp);
+        q.m_six_hsp = P(-6.f * f.hsp), q.m_hsq = P(-f.hsq);
+        q.Fx = P(f.Fx), q.Fy = P(f.Fy), q.rho_g = P(f.rho_g), q.inv_drho = P(1.0f / (f.rho_l - f.rho_g));
+        q.dnu = P(f.nu_l - f.nu_g), q.nu_g = P(f.nu_g), q.Lambda = P(f.Lambda);
+        q.m_b = P(-f.eos_b), q.b4 = P(f.eos_b * 0.25f), q.K = P(f.eos_K), q.RT = P(f.eos_RT), q.a = P(f.eos_a);
+        q.two_over_G = P(f.two_over_G);
+        q.inv_scale = P(f.inv_scale), q.scale = P(f.scale), q.m_scale = P(-f.scale), q.psi_s = P(f.psi_s);
+        q.rho_ref = P(f.rho_ref);
+        // 2^-k as FP16 (normal for k <= 14, subnormal down to 2^-24) or BF16 bits
+        const int kk = p.storage_scale_log2;
+        if (p.precision == LBM_BF16DEV) k.inv_scale_bits = (unsigned short)((127 - kk) << 7);
+        else k.inv_scale_bits = kk <= 14 ? (unsigned short)((15 - kk) << 10) : (unsigned short)(1u << (24 - kk));
+        for (int i = 0; i < 9; ++i) {
+            const float w = i == 0 ? 4.0f / 9.0f : (i <= 4 ? 1.0f / 9.0f : 1.0f / 36.0f);
+            const float wr = w * f.rho_ref;  // rounded like the kernels' w_i rho_ref
+            q.w[i] = P(w);
+            q.dec[i] = P(wr);
+            q.enc[i] = P(-(wr * f.scale));
+        }
+    }
     k.psi = c->psi;
     k.solid = c->solid;
     k.wall_u = c->wall_u;

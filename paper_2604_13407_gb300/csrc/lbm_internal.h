@@ -14,6 +14,20 @@ struct Consts {
     R hsp, hsq;  // 1 - s_p/2 and 1 - s_q/2 of the constant relaxation rates
 };
 
+// Constant operands of the packed FP32x2 kernel (k_fused2.cuh), each splatted to a pair
+// (c, c) on the host, so that the kernel never assembles a constant pair at run time.
+struct PairConsts {
+    float2 one, m_one, half, m_half, two, m_two, three, m_three, four, m_four, six, m_six;
+    float2 third, m_third, twelfth, ninth, w36, sixth, quarter;
+    float2 m_G, kq1, q2fac, kq7, c1G, m_c2G, sp, sq, hsp, hsq, six_hsp, m_six_hsp, m_hsq;
+    float2 Fx, Fy, rho_g, inv_drho, dnu, nu_g, Lambda;
+    float2 m_b, b4, K, RT, a, two_over_G;
+    float2 inv_scale, scale, m_scale, psi_s, rho_ref;
+    float2 dec[9];  // w_i rho_ref (decode of deviations)
+    float2 enc[9];  // -(w_i rho_ref) 2^k (encode of deviations)
+    float2 w[9];    // w_i
+};
+
 // Everything a kernel needs, passed by value.  Physical constants are kept in double
 // (host bookkeeping and the FP64 path) and, for kernels, in cd / cf by arithmetic type.
 struct KParams {
@@ -56,6 +70,8 @@ struct KParams {
     int *err;              // device error word (0 = fine)
     Consts<double> cd;     // constants for FP64 arithmetic
     Consts<float> cf;      // constants for FP32 arithmetic
+    PairConsts c2;         // the same as pairs, for the packed kernel
+    unsigned short inv_scale_bits;  // 2^-k in the storage type (FP16 or BF16 bits)
 };
 
 // Buffers and scalars of one transposed step.  Planes use the population row pitch.

@@ -49,6 +49,15 @@ def test_create_rejects_invalid_parameters(field, value):
     assert e.value.status == 1
 
 
+@pytest.mark.parametrize("k", [-16, 25])
+def test_create_rejects_fp16_scale_outside_the_fp16_range(k):
+    """FP16 deviation storage decodes with 2^-k held as an FP16 value: k in [-15, 24]."""
+    p = lbm.default_params(precision=lbm.F16DEV, storage_scale_log2=k)
+    with pytest.raises(lbm.LbmError) as e:
+        lbm.Simulation(p)
+    assert e.value.status == 1 and "storage_scale_log2" in str(e.value)
+
+
 def test_create_rejects_imaginary_pseudopotential():
     # rho_max past the point where p_EOS - rho/3 turns positive (psi^2 < 0)
     p = lbm.default_params(rho_max=0.9)
