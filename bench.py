@@ -29,6 +29,10 @@ RHO_G, RHO_L = 0.009291723294794338, 0.3581443962580134  # Maxwell densities of 
 T_07 = 0.7 * 0.3773 / 4.0
 TAU = 1.0
 BYTES = {"f64": 144, "f32": 72, "f16dev": 36, "bf16dev": 36}
+# DRAM bytes per lattice update of the packed fused kernel (k_fused2) at 8192 x 8192, from one ncu
+# launch list (dram__bytes_read.sum + dram__bytes_write.sum; profiles/k_fused2_*_spinodal.md).
+# Valid for the kernel as captured; set to None when the kernel changes until it is captured again.
+TRAFFIC_PER_UPDATE = {"f32": 72.6, "f16dev": 36.1}
 HBM_FALLBACK = 6800.0
 
 
@@ -185,6 +189,50 @@ def e2e_glups(n, precision, steps, rho_host):
     return n * n * steps / t / 1e9, 8 * n * n / steps, 3 * 8 * n * n / steps
 
 
+def adjoint_cost(precision, nsteps, checkpoint_every=200):
+    """Adjoint workload: 256 x 1024 channel (walls at x = -1/2 and 255.5, periodic in y),
+    radius-20 droplet at a seed-4 jittered centre near (128, 900), buoyant gravity
+    g = (0, -2e-6), improved scheme.  Times nsteps forward steps and lbm_adjoint_step over
+    the same nsteps (forward sweep, segment recompute and transposed steps; objective: the
+    y force on the walls; buffers already allocated by a first call) with CUDA events;
+    returns the per-step times and their ratio."""
+    import torch
+    from paper_2604_13407_gb300 import inputs as I
+    from paper_2604_13407_gb300 import lbm
+    nx, ny = 256, 1024
+    cx, cy = I.jittered_centre(4, 128.0, 900.0)
+    rho = I.droplet(nx, ny, RHO_L, RHO_G, 20.0, cx, cy, periodic_x=False, periodic_y=True)
+
+    def sim():
+        p = lbm.default_params(nx=nx, ny=ny, periodic_x=0, periodic_y=1, precision=precision, scheme=1,
+                               force_mode=lbm.FORCE_BUOYANT, Fx=0.0, Fy=-2e-6, T=T_07, rho_l=RHO_L,
+                               rho_g=RHO_G, rho_s=RHO_G, tau_l=0.8, tau_g=0.8)
+        s = lbm.Simulation(p, stream=torch.cuda.current_stream())
+        s.init_fields(rho)
+        return s
+
+    out = {}
+    for name in ("forward", "adjoint"):
+        s = sim()
+        if name == "forward":
+            s.step(3)
+        else:
+            s.adjoint(nsteps, checkpoint_every, lbm.OBJ_WALL_FORCE_Y)  # allocates the checkpoint buffers
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        if name == "forward":
+            s.step(nsteps)
+        else:
+            s.adjoint(nsteps, checkpoint_every, lbm.OBJ_WALL_FORCE_Y)
+        e1.record()
+        torch.cuda.synchronize()
+        out[name] = e0.elapsed_time(e1) / nsteps
+        s.close()
+    return {"forward_ms_per_step": out["forward"], "adjoint_ms_per_step": out["adjoint"],
+            "ratio": out["adjoint"] / out["forward"], "steps": nsteps, "checkpoint_every": checkpoint_every}
+
+
 # ------------------------------------------------------------ CPU legs ----
 
 def oracle_glups(n, seconds_target=10.0, max_steps=50):
@@ -245,6 +293,7 @@ def main():
     ap.add_argument("--cpu-baseline", type=int, default=1)
     ap.add_argument("--ref-sample", type=int, default=512)
     ap.add_argument("--e2e", type=int, default=1)
+    ap.add_argument("--adjoint", type=int, default=1, help="also time the adjoint against the forward step")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -301,7 +350,16 @@ def main():
             variants[name] = {"GLUPS": n * n * k / t2 / 1e9, "bytes_per_update": b,
                               "achieved_GBs": b * n * n / tl / 1e9, "frac": b * n * n / tl / 1e9 / hbm,
                               "kernel": "fused" if s2.kernel_in_use == lbm.KERNEL_FUSED else "two_pass"}
+            if prec == "f64":
+                # FP64-ALU bound: ncu shows the FP64 pipe 85% busy and DRAM at 1.4% (k_fused_f64 profile)
+                variants[name]["bound"] = "fp64 alu"
             s2.close()
+
+    adjoint = None
+    if args.adjoint and rank == 0 and not dist_on:
+        adjoint = {"workload": "droplet in a 256x1024 channel (radius 20, buoyant g 2e-6, walls in x, periodic y), "
+                               "objective: time-averaged y force on the walls, gradient wrt (Fx, Fy, G, T)",
+                   "f32": adjoint_cost(lbm.F32, 2000), "f64": adjoint_cost(lbm.F64, 400)}
 
     e2e = None
     if rank == 0 and args.e2e:
@@ -324,11 +382,15 @@ def main():
                        "l2": "inputs larger than L2 (population buffers %.1f GB each)" % (bpu / 2 * n * n / 1e9),
                        "parallelism": "replicas" if world > 1 else "single"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                         "frac": achieved / hbm, "traffic": None, "peak_kind": peak_kind,
+                         "frac": achieved / hbm, "peak_kind": peak_kind,
+                         "traffic": (TRAFFIC_PER_UPDATE[args.precision] * n * n
+                                     if kernels_per_step == 1 and n == 8192 and TRAFFIC_PER_UPDATE.get(args.precision)
+                                     else None),
+                         "traffic_unit": "bytes per launch (ncu, 8192x8192)",
                          "bytes_per_update": bpu,
                          "kernel": "fused" if kernels_per_step == 1 else "two_pass (step)"},
             "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": args.steps * kernels_per_step,
-            "clocks": clocks, "variants": variants,
+            "clocks": clocks, "variants": variants, "adjoint": adjoint,
             "mass": d[0],
         }
         print(json.dumps(line))

@@ -128,19 +128,45 @@ __device__ __forceinline__ double warp_max(double v)
 
 constexpr int kDiagSums = 9;
 
-// FP64 diagnostics (see lbm_get_diagnostics): warp-shuffle sums, then one FP64 atomic
-// per block and quantity.  max |u| uses the ordering of non-negative doubles' bits.
+// Per-thread sum of FP32-arithmetic kernels: compensated (Knuth's TwoSum), so that the
+// pair (s, c) carries the sum of the added floats to about 2^-48 relative, and converted
+// to FP64 once; FP64 arithmetic kernels sum in FP64 directly.  (GB300 runs FP32 adds at
+// many times the FP64 rate.)
+template <class R>
+struct DiagAcc {
+    double s = 0.0;
+    __device__ __forceinline__ void add(R x) { s += double(x); }
+    __device__ __forceinline__ double value() const { return s; }
+};
+template <>
+struct DiagAcc<float> {
+    float s = 0.f, c = 0.f;
+    __device__ __forceinline__ void add(float x)
+    {
+        const float t = s + x, z = t - s;
+        c += (s - (t - z)) + (x - z);
+        s = t;
+    }
+    __device__ __forceinline__ double value() const { return double(s) + double(c); }
+};
+
+// FP64 diagnostics (see lbm_get_diagnostics): a grid-stride pass over all nodes, each
+// thread accumulating its nodes (DiagAcc), then FP64 warp-shuffle and block sums and one
+// FP64 atomic per block and quantity.  max |u| uses the ordering of non-negative doubles'
+// bits.
 template <class S>
 __global__ void __launch_bounds__(kRowThreads) k_diag(KParams kp, double *acc, unsigned long long *umax, int *nan_count)
 {
     typedef typename Codec<S>::R R;
     __shared__ double red[kRowThreads / 32][kDiagSums + 1];
-    const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y;
-    double v[kDiagSums + 1];
-#pragma unroll
-    for (int k = 0; k <= kDiagSums; ++k) v[k] = 0.0;
-    const int64_t node = (int64_t)y * kp.nx + x;
-    if (x < kp.nx && !node_is_solid(kp, node)) {
+    DiagAcc<R> a[kDiagSums];
+    R umax_t = R(0);
+    const int64_t n = (int64_t)kp.nx * kp.ny;
+    const R half_lg = R(0.5 * (kp.rho_l + kp.rho_g));
+    int bad = 0;
+    for (int64_t node = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; node < n; node += (int64_t)gridDim.x * blockDim.x) {
+        if (node_is_solid(kp, node)) continue;
+        const int y = (int)(node / kp.nx), x = (int)(node - (int64_t)y * kp.nx);
         const R *psi = static_cast<const R *>(kp.psi);
         R f[9], fb[9], Sx, Sy, Fex, Fey, ux, uy;
         R mom[2] = {R(0), R(0)};
@@ -150,23 +176,26 @@ __global__ void __launch_bounds__(kRowThreads) k_diag(KParams kp, double *acc, u
         external_force<R>(kp, node, rho, Fex, Fey);
         collide<R>(kp, f, rho, psi[node], Sx, Sy, Fex, Fey, fb, ux, uy);
         const R G = cst<R>(kp).G;
-        const double jx = double(((f[1] - f[3]) + (f[5] - f[6])) + (f[8] - f[7]));
-        const double jy = double(((f[2] - f[4]) + (f[5] + f[6])) - (f[7] + f[8]));
-        v[0] = double(rho);
-        v[1] = jx;
-        v[2] = jy;
-        v[3] = double(-G * psi[node] * Sx + Fex);
-        v[4] = double(-G * psi[node] * Sy + Fey);
-        v[5] = double(mom[0]);
-        v[6] = double(mom[1]);
-        if (double(rho) > 0.5 * (kp.rho_l + kp.rho_g)) {
-            v[7] = double(rho) * double(uy);
-            v[8] = double(rho);
+        a[0].add(rho);
+        a[1].add(((f[1] - f[3]) + (f[5] - f[6])) + (f[8] - f[7]));
+        a[2].add(((f[2] - f[4]) + (f[5] + f[6])) - (f[7] + f[8]));
+        a[3].add(-G * psi[node] * Sx + Fex);
+        a[4].add(-G * psi[node] * Sy + Fey);
+        a[5].add(mom[0]);
+        a[6].add(mom[1]);
+        if (rho > half_lg) {
+            a[7].add(rho * uy);
+            a[8].add(rho);
         }
-        const double um = sqrt(double(ux) * double(ux) + double(uy) * double(uy));
-        v[9] = um;
-        if (!isfinite(double(rho)) || !isfinite(um)) atomicAdd(nan_count, 1);
+        const R um = sqrt(ux * ux + uy * uy);
+        umax_t = um > umax_t ? um : umax_t;
+        if (!isfinite(double(rho)) || !isfinite(double(um))) bad = 1;
     }
+    double v[kDiagSums + 1];
+#pragma unroll
+    for (int k = 0; k < kDiagSums; ++k) v[k] = a[k].value();
+    v[kDiagSums] = double(umax_t);
+    if (bad) atomicAdd(nan_count, 1);
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
 #pragma unroll
     for (int k = 0; k < kDiagSums; ++k) v[k] = warp_sum(v[k]);
@@ -235,7 +264,13 @@ struct TwoPass {
     }
     static cudaError_t diag(const KParams &kp, double *acc, unsigned long long *umax, int *nanc, cudaStream_t st)
     {
-        k_diag<S><<<row_grid(kp), kRowThreads, 0, st>>>(kp, acc, umax, nanc);
+        int dev = 0, sms = 148;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        const int64_t n = (int64_t)kp.nx * kp.ny;
+        int64_t blocks = (n + kRowThreads - 1) / kRowThreads;
+        if (blocks > 8 * (int64_t)sms) blocks = 8 * (int64_t)sms;
+        k_diag<S><<<(unsigned)blocks, kRowThreads, 0, st>>>(kp, acc, umax, nanc);
         return cudaGetLastError();
     }
     static cudaError_t get_state(const KParams &kp, double *out, cudaStream_t st)
