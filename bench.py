@@ -294,11 +294,20 @@ def main():
     ap.add_argument("--ref-sample", type=int, default=512)
     ap.add_argument("--e2e", type=int, default=1)
     ap.add_argument("--adjoint", type=int, default=1, help="also time the adjoint against the forward step")
+    ap.add_argument("--adjoint-only", type=int, default=0,
+                    help="time only the adjoint against the forward step (one JSON line; for profiling)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
     if args.impl == "reference":
         return run_reference(args)
+    if args.adjoint_only:
+        import torch
+        from paper_2604_13407_gb300 import lbm
+        torch.cuda.set_device(0)
+        prec = {"f64": lbm.F64, "f32": lbm.F32}[args.precision]
+        print(json.dumps({"adjoint": adjoint_cost(prec, args.steps), "precision": args.precision}))
+        return
 
     import torch
     from paper_2604_13407_gb300 import lbm

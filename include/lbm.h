@@ -217,9 +217,10 @@ LBM_API lbm_status lbm_set_param(lbm_ctx *ctx, int32_t which, double value);
  * Supported: FP64 and FP32 storage, periodic directions, resting half-way walls (domain
  * edges and solid nodes), CONST and BUOYANT forces, one or two relaxation times;
  * LBM_ENOTSUP otherwise.  Device memory (allocated on the first call, kept until
- * lbm_destroy or a larger call): ceil(nsteps/K) + K - 1 population states, K psi fields
- * and 15 planes of the arithmetic type, K = min(checkpoint_every, nsteps); LBM_ENOMEM
- * when it does not fit (lower checkpoint_every).  LBM_EINVAL: nsteps or
+ * lbm_destroy or a larger call): ceil(nsteps/K) + 2 (K - 1) population states, 2 K psi
+ * fields and 15 planes of the arithmetic type, K = min(checkpoint_every, nsteps) (the
+ * recompute of a segment overlaps, on a second stream, the transposed steps of the segment
+ * after it); LBM_ENOMEM when it does not fit (lower checkpoint_every).  LBM_EINVAL: nsteps or
  * checkpoint_every < 1, unknown objective. */
 LBM_API lbm_status lbm_adjoint_step(lbm_ctx *ctx, int64_t nsteps, int32_t checkpoint_every,
                             int32_t objective, double *J, double grad[4], double *lambda0);

@@ -87,25 +87,22 @@ __device__ __forceinline__ void p_eos_derivs(const KParams &kp, R rho, R &p_rho,
     p_T = c.eos_K * rho * c.eos_R * g;
 }
 
-template <class R>
-__device__ __forceinline__ void block_add4(double v0, double v1, double v2, double v3, double *acc)
+// Block sum of N per-thread doubles, added to acc[0..N-1] with one FP64 atomic each.
+template <int N>
+__device__ __forceinline__ void block_add(const double (&v)[N], double *acc)
 {
-    __shared__ double red[kRowThreads / 32][4];
-    v0 = warp_sum(v0);
-    v1 = warp_sum(v1);
-    v2 = warp_sum(v2);
-    v3 = warp_sum(v3);
+    __shared__ double red[kRowThreads / 32][N];
+    double w[N];
+#pragma unroll
+    for (int k = 0; k < N; ++k) w[k] = warp_sum(v[k]);
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    if (lane == 0) {
-        red[wid][0] = v0;
-        red[wid][1] = v1;
-        red[wid][2] = v2;
-        red[wid][3] = v3;
-    }
+    if (lane == 0)
+#pragma unroll
+        for (int k = 0; k < N; ++k) red[wid][k] = w[k];
     __syncthreads();
-    if (threadIdx.x < 4) {
+    if (threadIdx.x < N) {
         double s = 0.0;
-        for (int w = 0; w < kRowThreads / 32; ++w) s += red[w][threadIdx.x];
+        for (int q = 0; q < kRowThreads / 32; ++q) s += red[q][threadIdx.x];
         if (s != 0.0) atomicAdd(acc + threadIdx.x, s);
     }
 }
@@ -117,7 +114,7 @@ __global__ void __launch_bounds__(kRowThreads) k_adj1(KParams kp, AdjArgs aa)
     typedef typename Codec<S>::R R;
     const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y;
     const int64_t node = (int64_t)y * kp.nx + x, k = (int64_t)y * kp.pitch + x;
-    double gFx = 0.0, gFy = 0.0, gG = 0.0, gT = 0.0;
+    double gFx = 0.0, gFy = 0.0, gG = 0.0, gT = 0.0, Jt = 0.0;
     if (x < kp.nx && !node_is_solid(kp, node)) {
         const Consts<R> &cc = cst<R>(kp);
         R lam[9];
@@ -129,6 +126,22 @@ __global__ void __launch_bounds__(kRowThreads) k_adj1(KParams kp, AdjArgs aa)
         const R rho = density<R>(f);
         const R jx = ((f[1] - f[3]) + (f[5] - f[6])) + (f[8] - f[7]);
         const R jy = ((f[2] - f[4]) + (f[5] + f[6])) - (f[7] + f[8]);
+        if (aa.J != nullptr) {
+            // <W, A_t> at this node from its pulled populations: a population stored at x that
+            // the next streaming sends into a wall is pulled back by x itself as f_i with
+            // x - e_i a wall; every other one is pulled by exactly one fluid node
+            R wall_y = R(0), wall_x = R(0);
+#pragma unroll
+            for (int i = 1; i < 9; ++i) {
+                int xs = x - ex_(i), ys = y - ey_(i);
+                const bool wall = !wrap_xy(kp, xs, ys) || (kp.solid != nullptr && kp.solid[(int64_t)ys * kp.nx + xs] != 0);
+                if (wall) {
+                    wall_x += R(ex_(i)) * f[i];
+                    wall_y += R(ey_(i)) * f[i];
+                }
+            }
+            Jt = aa.objective == 0 ? double(R(-2) * wall_y) : double(jx - R(2) * wall_x) * aa.inv_nfluid;
+        }
         const R *psif = static_cast<const R *>(kp.psi);
         const R psi = psif[node];
         R Sx, Sy, Fex, Fey;
@@ -277,7 +290,13 @@ __global__ void __launch_bounds__(kRowThreads) k_adj1(KParams kp, AdjArgs aa)
         static_cast<R *>(aa.dpsi)[k] = dpsi_loc;
         static_cast<R *>(aa.rho)[k] = rho;
     }
-    block_add4<R>(gFx, gFy, gG, gT, aa.grad);
+    if (aa.J != nullptr) {
+        const double v[5] = {gFx, gFy, gG, gT, Jt};
+        block_add<5>(v, aa.grad);  // aa.J == aa.grad + 4
+    } else {
+        const double v[4] = {gFx, gFy, gG, gT};
+        block_add<4>(v, aa.grad);
+    }
 }
 
 // Pass 2: dJ/dpsi(x) from the stencils that read psi(x), then c(x) = psi'(rho) dJ/dpsi.
@@ -311,7 +330,8 @@ __global__ void __launch_bounds__(kRowThreads) k_adj2(KParams kp, AdjArgs aa)
         gT = double(p_T / Gpsi * dpsi);
         gG = double(-psi / (R(2) * cc.G) * dpsi);
     }
-    block_add4<R>(0.0, 0.0, gG, gT, aa.grad);
+    const double v[4] = {0.0, 0.0, gG, gT};
+    block_add<4>(v, aa.grad);
 }
 
 // lambda_0 = dJ/dA at the starting state (no objective weight at t = 0), FP64 [9][ny][nx].
@@ -353,7 +373,8 @@ __global__ void __launch_bounds__(kRowThreads) k_objective(KParams kp, int objec
             if (w != 0.0) v += w * double(load_pop<S>(kp, i, x, y));
         }
     }
-    block_add4<R>(v, 0.0, 0.0, 0.0, acc);
+    const double vv[1] = {v};
+    block_add<1>(vv, acc);
 }
 
 template <class S>

@@ -7,12 +7,15 @@
 //   lambda_0 = Step'(A_0)^T lambda_1,  dJ/dtheta = sum_t (dStep(A_t)/dtheta)^T lambda_{t+1}.
 //
 // Forward sweep: the context advances n steps with its normal kernels, storing A_t every
-// K steps (a checkpoint) and summing <W, A_t> in FP64.  Backward sweep, one segment of K
+// K steps (a checkpoint); <W, A_n> is summed in FP64 there, <W, A_t> of the other states by
+// the transposed passes (objective alone: every state in the forward sweep).  Backward sweep, one segment of K
 // steps at a time from the last: the states of the segment are recomputed from its
 // checkpoint with the two-pass step (whose psi pass leaves the psi field of each state in
 // a buffer of its own), then the transposed step runs from the last state of the segment
-// to the first.  Device memory: ceil(n/K) checkpoints, K - 1 segment states, K psi
-// fields and the adjoint planes; it is kept for the next call with the same sizes.
+// to the first.  The recompute of a segment runs on a second stream, overlapping the
+// transposed steps of the segment after it, so segment states and psi fields come in two
+// sets.  Device memory: ceil(n/K) checkpoints, 2 (K - 1) segment states, 2 K psi fields
+// and the adjoint planes; it is kept for the next call with the same sizes.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -26,12 +29,19 @@ namespace lbm {
 struct AdjointState {
     void *base = nullptr;
     size_t bytes = 0;
+    cudaStream_t side = nullptr;  // recomputes the next segment while the transposed steps run
+    cudaEvent_t fork = nullptr, recomputed[2] = {nullptr, nullptr}, reversed[2] = {nullptr, nullptr};
 };
 
 void adjoint_free(AdjointState *a)
 {
     if (!a) return;
+    if (a->side) cudaStreamSynchronize(a->side);
     if (a->base) cudaFree(a->base);
+    cudaEvent_t evs[] = {a->fork, a->recomputed[0], a->recomputed[1], a->reversed[0], a->reversed[1]};
+    for (cudaEvent_t e : evs)
+        if (e) cudaEventDestroy(e);
+    if (a->side) cudaStreamDestroy(a->side);
     delete a;
 }
 
@@ -49,7 +59,7 @@ struct Carver {
 };
 
 struct Layout {
-    std::vector<void *> ckpt, seg, psi;
+    std::vector<void *> ckpt, seg[2], psi[2];  // two sets of segment states and psi fields
     void *g[2], *c[2], *dS, *dpsi, *rho;
     double *acc;
 };
@@ -57,11 +67,13 @@ struct Layout {
 size_t carve(Carver &cv, Layout &L, int64_t nseg, int64_t K, size_t state_bytes, size_t plane_r, size_t psi_bytes)
 {
     L.ckpt.resize(nseg);
-    L.seg.resize(std::max<int64_t>(K - 1, 1));
-    L.psi.resize(K);
     for (auto &b : L.ckpt) b = cv.take(state_bytes);
-    for (auto &b : L.seg) b = cv.take(state_bytes);
-    for (auto &b : L.psi) b = cv.take(psi_bytes);
+    for (int q = 0; q < 2; ++q) {
+        L.seg[q].resize(std::max<int64_t>(K - 1, 1));
+        L.psi[q].resize(K);
+        for (auto &b : L.seg[q]) b = cv.take(state_bytes);
+        for (auto &b : L.psi[q]) b = cv.take(psi_bytes);
+    }
     for (int s = 0; s < 2; ++s) {
         L.g[s] = cv.take(9 * plane_r);
         L.c[s] = cv.take(plane_r);
@@ -146,6 +158,11 @@ lbm_status adjoint_run(lbm_ctx *ctx, int64_t nsteps, int32_t K, int32_t objectiv
     Carver cv{static_cast<char *>(as->base)};
     if (backward) carve(cv, L, nseg, Kseg, state_bytes, plane_r, psi_bytes);
     else carve(cv, L, 0, 1, 0, 0, 0);
+    if (backward && !as->side) {
+        ACK(cudaStreamCreateWithFlags(&as->side, cudaStreamNonBlocking), "cudaStreamCreate");
+        cudaEvent_t *evs[] = {&as->fork, &as->recomputed[0], &as->recomputed[1], &as->reversed[0], &as->reversed[1]};
+        for (cudaEvent_t *e : evs) ACK(cudaEventCreateWithFlags(e, cudaEventDisableTiming), "cudaEventCreate");
+    }
 
     const double inv_nfluid = 1.0 / double(v.n_fluid);
     const double w = 1.0 / double(nsteps);
@@ -162,8 +179,12 @@ lbm_status adjoint_run(lbm_ctx *ctx, int64_t nsteps, int32_t K, int32_t objectiv
             msg = "forward step failed";
             return s;
         }
-        kq.src = v.pops[*v.cur];
-        ACK(v.L->objective(kq, objective, inv_nfluid, L.acc, st), "objective kernel");
+        // with a backward sweep, <W, A_t> of t = 1 .. n-1 is summed by the transposed passes,
+        // which read those states anyway; only the last state is summed here
+        if (!backward || t == nsteps - 1) {
+            kq.src = v.pops[*v.cur];
+            ACK(v.L->objective(kq, objective, inv_nfluid, L.acc, st), "objective kernel");
+        }
     }
 
     if (!backward) {
@@ -185,31 +206,50 @@ lbm_status adjoint_run(lbm_ctx *ctx, int64_t nsteps, int32_t K, int32_t objectiv
     aa.rho = L.rho;
     int gi = 0;  // buffer holding (g, c) of the step after; none before the first reversal
     bool have_next = false;
-    for (int64_t s = nseg - 1; s >= 0; --s) {
+    // Segment s is recomputed on the side stream into buffer set s & 1 while the transposed
+    // steps of segment s + 1 run on the context stream from set (s + 1) & 1; events order a
+    // set's reuse after the transposed steps that read it.
+    auto recompute = [&](int64_t s) -> lbm_status {
+        const int q = (int)(s & 1);
         const int64_t t0 = s * K, t1 = std::min<int64_t>((s + 1) * K, nsteps);
-        auto state = [&](int64_t t) -> void * { return t == t0 ? L.ckpt[s] : L.seg[t - t0 - 1]; };
+        if (s + 2 < nseg) ACK(cudaStreamWaitEvent(as->side, as->reversed[q], 0), "event wait");
         KParams kp = *v.kp;
         for (int64_t t = t0; t < t1; ++t) {
-            kp.src = state(t);
-            kp.psi = L.psi[t - t0];
-            ACK(v.psi_pass(kp, st), "psi kernel");
+            kp.src = t == t0 ? L.ckpt[s] : L.seg[q][t - t0 - 1];
+            kp.psi = L.psi[q][t - t0];
+            ACK(v.psi_pass(kp, as->side), "psi kernel");
             if (t + 1 < t1) {
-                kp.dst = state(t + 1);
-                ACK(v.collide_pass(kp, st), "collide kernel");
+                kp.dst = L.seg[q][t - t0];
+                ACK(v.collide_pass(kp, as->side), "collide kernel");
             }
         }
+        ACK(cudaEventRecord(as->recomputed[q], as->side), "event record");
+        return LBM_OK;
+    };
+    ACK(cudaEventRecord(as->fork, st), "event record");
+    ACK(cudaStreamWaitEvent(as->side, as->fork, 0), "event wait");
+    lbm_status rs = recompute(nseg - 1);
+    if (rs != LBM_OK) return rs;
+    for (int64_t s = nseg - 1; s >= 0; --s) {
+        const int q = (int)(s & 1);
+        const int64_t t0 = s * K, t1 = std::min<int64_t>((s + 1) * K, nsteps);
+        if (s > 0 && (rs = recompute(s - 1)) != LBM_OK) return rs;
+        ACK(cudaStreamWaitEvent(st, as->recomputed[q], 0), "event wait");
+        KParams kp = *v.kp;
         for (int64_t t = t1 - 1; t >= t0; --t) {
-            kp.src = state(t);
-            kp.psi = L.psi[t - t0];
+            kp.src = t == t0 ? L.ckpt[s] : L.seg[q][t - t0 - 1];
+            kp.psi = L.psi[q][t - t0];
             aa.g_in = have_next ? L.g[gi] : nullptr;
             aa.c_in = have_next ? L.c[gi] : nullptr;
             aa.g_out = L.g[gi ^ 1];
             aa.c_out = L.c[gi ^ 1];
+            aa.J = t >= 1 ? L.acc + 5 : nullptr;  // pass 1 adds <W, A_t> at grad + 4 = acc + 5
             ACK(v.L->adj_pass1(kp, aa, st), "adjoint pass 1");
             ACK(v.L->adj_pass2(kp, aa, st), "adjoint pass 2");
             gi ^= 1;
             have_next = true;
         }
+        ACK(cudaEventRecord(as->reversed[q], st), "event record");
     }
 
     if (lambda0) {
@@ -228,7 +268,7 @@ lbm_status adjoint_run(lbm_ctx *ctx, int64_t nsteps, int32_t K, int32_t objectiv
     double h[8];
     ACK(cudaMemcpyAsync(h, L.acc, sizeof h, cudaMemcpyDeviceToHost, st), "D2H");
     ACK(cudaStreamSynchronize(st), "adjoint");
-    *J = h[0] * w;
+    *J = (h[0] + h[5]) * w;
     if (grad)
         for (int k = 0; k < 4; ++k) grad[k] = h[1 + k];
     return v.check_error(ctx, msg);

@@ -87,6 +87,7 @@ struct AdjArgs {
     int objective;      // 0: y momentum handed to the walls by the next streaming; 1: mean j_x
     double inv_nfluid;  // 1 / number of fluid nodes (objective 1)
     double *grad;       // FP64 accumulators: dJ/dFx, dJ/dFy, dJ/dG, dJ/dT
+    double *J;          // FP64 accumulator of <W, A_t> for the state of pass 1 (null: not summed)
 };
 
 // Storage precisions (match lbm_precision)
