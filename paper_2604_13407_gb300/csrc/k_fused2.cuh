@@ -267,22 +267,25 @@ __device__ __forceinline__ void external_force_pair(const KParams &kp, int64_t n
     {                                                                                                         \
         constexpr int d_ = 1 - ey_(I), off_ = -ex_(I), wc_ = I == 0 ? 0 : (I <= 4 ? 1 : 5);                  \
         if constexpr (IsDev<S>::value) {                                                                      \
-            const v2 wref = kp.per_node_ref ? v2{kp.c2.w[wc_]} * load_ref_pair(ref[d_], off_) : v2{kp.c2.dec[wc_]}; \
+            const v2 wref = O::per_node_ref(kp) ? v2{kp.c2.w[wc_]} * load_ref_pair(ref[d_], off_) : v2{kp.c2.dec[wc_]}; \
             f_new[I] = Pair2<S>::template dec<off_>(row[d_] + I * W, wref, kp.inv_scale_bits);               \
         } else {                                                                                              \
             f_new[I] = Pair2<S>::template load<off_>(row[d_] + I * W);                                       \
         }                                                                                                     \
     }
 
+#ifndef LBM_FUSED2_MINB
+#define LBM_FUSED2_MINB 2  // CTAs per SM the register allocation must allow
+#endif
 template <class S, int NW, int RING, bool PERIODIC, class O>
-__global__ void __launch_bounds__(32 * (NW + 1), 2) k_fused2(KParams kp, int seg_rows)
+__global__ void __launch_bounds__(32 * (NW + 1), LBM_FUSED2_MINB) k_fused2(KParams kp, int seg_rows)
 {
     typedef FusedLayout2<S, NW, RING> L;
     constexpr int TX = L::TX, HX = L::HX, W = L::W;
     constexpr uint32_t ES = sizeof(S);
     extern __shared__ __align__(128) unsigned char smem[];
     unsigned char *pops = smem;
-    const bool has_ref = kp.per_node_ref != 0;
+    const bool has_ref = O::per_node_ref(kp);
     float *refs = has_ref ? reinterpret_cast<float *>(smem + (size_t)RING * L::POP_ROW) : nullptr;
     uint64_t *full = reinterpret_cast<uint64_t *>(smem + L::in_bytes(has_ref));
     uint64_t *empty = full + RING;
@@ -407,8 +410,8 @@ __global__ void __launch_bounds__(32 * (NW + 1), 2) k_fused2(KParams kp, int seg
                         const S *a = row[1] + o * W;
                         float r0 = Pair2<S>::load1(a), r1 = Pair2<S>::load1(a + 1);
                         if (dev) {
-                            const float rf0 = kp.per_node_ref ? ref[1][0] : rho_ref;
-                            const float rf1 = kp.per_node_ref ? ref[1][1] : rho_ref;
+                            const float rf0 = has_ref ? ref[1][0] : rho_ref;
+                            const float rf1 = has_ref ? ref[1][1] : rho_ref;
                             r0 = r0 * inv_scale + w_<float>(o) * rf0;
                             r1 = r1 * inv_scale + w_<float>(o) * rf1;
                         }
@@ -503,13 +506,17 @@ struct Fused2 {
         k_fused2<S, NW, RING, P, O><<<dim3(strips, nseg), 32 * (NW + 1), L::bytes(kp.per_node_ref != 0), st>>>(kp, seg_rows);
         return cudaGetLastError();
     }
+    // Fully periodic lattices with a constant force and one relaxation time get
+    // instantiations with those options (and the reference-density mode) fixed at compile
+    // time; everything else reads them at run time.
     static cudaError_t launch(const KParams &kp, cudaStream_t st)
     {
-        if (kp.periodic_x && kp.periodic_y) {
-            if (kp.force_mode == 0 && !kp.var_tau)
-                return kp.improved ? launch_one<true, Opts<1, 0, 0>>(kp, st) : launch_one<true, Opts<0, 0, 0>>(kp, st);
-            return launch_one<true, RuntimeOpts>(kp, st);
+        if (kp.periodic_x && kp.periodic_y && kp.force_mode == 0 && !kp.var_tau) {
+            if (IsDev<S>::value && kp.per_node_ref)
+                return kp.improved ? launch_one<true, Opts<1, 0, 0, 1>>(kp, st) : launch_one<true, Opts<0, 0, 0, 1>>(kp, st);
+            return kp.improved ? launch_one<true, Opts<1, 0, 0, 0>>(kp, st) : launch_one<true, Opts<0, 0, 0, 0>>(kp, st);
         }
+        if (kp.periodic_x && kp.periodic_y) return launch_one<true, RuntimeOpts>(kp, st);
         return launch_one<false, RuntimeOpts>(kp, st);
     }
 };

@@ -35,11 +35,12 @@ template <class R>
 constexpr bool is_f64() { return std::is_same<R, double>::value; }
 
 // Options a kernel may fix at compile time; -1 means "read from KParams at run time".
-template <int IMPROVED = -1, int VAR_TAU = -1, int FORCE_MODE = -1>
+template <int IMPROVED = -1, int VAR_TAU = -1, int FORCE_MODE = -1, int NODE_REF = -1>
 struct Opts {
     static __device__ __forceinline__ bool improved(const KParams &kp) { return IMPROVED >= 0 ? IMPROVED != 0 : kp.improved != 0; }
     static __device__ __forceinline__ bool var_tau(const KParams &kp) { return VAR_TAU >= 0 ? VAR_TAU != 0 : kp.var_tau != 0; }
     static __device__ __forceinline__ int force_mode(const KParams &kp) { return FORCE_MODE >= 0 ? FORCE_MODE : kp.force_mode; }
+    static __device__ __forceinline__ bool per_node_ref(const KParams &kp) { return NODE_REF >= 0 ? NODE_REF != 0 : kp.per_node_ref != 0; }
 };
 typedef Opts<> RuntimeOpts;
 
