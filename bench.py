@@ -144,10 +144,22 @@ def timed_steps(sim, steps, warmup, dist_on):
         torch.distributed.barrier()
     t = e0.elapsed_time(e1) / 1e3
     if dist_on:
-        tt = torch.tensor([t], device="cuda", dtype=torch.float64)
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        t = float(tt.item())
+        t = max_over_ranks(t)
     return t
+
+
+def max_over_ranks(t):
+    """The largest of the ranks' times (the job ends when the slowest rank ends)."""
+    import torch
+    dev = "cuda" if torch.distributed.get_backend() == "nccl" else "cpu"
+    tt = torch.tensor([t], device=dev, dtype=torch.float64)
+    torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+    return float(tt.item())
+
+
+def job_updates(n, steps, world):
+    """Lattice updates of the whole job: every rank advances its own n x n replica (weak scaling)."""
+    return float(n) * n * steps * world
 
 
 def per_launch_time(sim, launches=20):
@@ -229,8 +241,11 @@ def adjoint_cost(precision, nsteps, checkpoint_every=200):
         torch.cuda.synchronize()
         out[name] = e0.elapsed_time(e1) / nsteps
         s.close()
+    # lbm_adjoint_step advances the state like lbm_step; what it adds is the backward part
+    back = out["adjoint"] - out["forward"]
     return {"forward_ms_per_step": out["forward"], "adjoint_ms_per_step": out["adjoint"],
-            "ratio": out["adjoint"] / out["forward"], "steps": nsteps, "checkpoint_every": checkpoint_every}
+            "ratio": out["adjoint"] / out["forward"], "backward_ms_per_step": back,
+            "backward_ratio": back / out["forward"], "steps": nsteps, "checkpoint_every": checkpoint_every}
 
 
 # ------------------------------------------------------------ CPU legs ----
@@ -338,7 +353,7 @@ def main():
     t_launch = per_launch_time(sim)
     d = sim.diagnostics()
     sim.close()
-    updates = float(n) * n * args.steps * world
+    updates = job_updates(n, args.steps, world)
     value = updates / t / 1e9
     bpu = BYTES[args.precision]
     achieved = bpu * n * n / t_launch / 1e9

@@ -44,7 +44,7 @@ def test_fp64_auto_kernel_matches_oracle(name, oracle_runs):
 @pytest.mark.parametrize("name", sorted(CASES))
 def test_fp32_matches_oracle(name, oracle_runs):
     """FP32: max |du| <= 1e-4 max(max |u|, 1e-3) (FP32 resolves u to ~1e-8 absolute at
-    these densities, so a near-static case is judged against 1e-3) and rho within 1e-3."""
+    these densities, so a near-static case is compared against 1e-3) and rho within 1e-3."""
     c = CASES[name]
     sim = GC.run_gpu(c, lbm.F32)
     rg, ug, vg = sim.moments()
@@ -123,6 +123,30 @@ def test_diagnostics_match_oracle(name, oracle_runs):
     assert abs(dg[8] - do[8]) < 1e-12 * do[0]
     assert abs(dg[9] - do[9]) < 1e-10 * do[9]
     assert np.abs(dg[1:8] - do[1:8]).max() < 1e-12 * do[0], (dg, do)
+
+
+def test_fp32_diagnostics_sum_the_fp32_state_exactly():
+    """FP32 storage: the diagnostics add the per-node FP32 densities of the kernel (pulled
+    populations summed in the kernel's order) with compensated per-thread sums and FP64
+    across threads, so the mass equals the exact sum of those FP32 densities to ~1e-14."""
+    import math
+    c = CASES["droplet"]  # periodic in x and y: the pull is a permutation
+    sim = GC.run_gpu(c, lbm.F32, steps=30)
+    A = sim.get_state().astype(np.float32)
+    f = [np.roll(np.roll(A[i], lbm_ey(i), axis=0), lbm_ex(i), axis=1) for i in range(9)]
+    rho = (((f[0] + f[1]) + (f[2] + f[3])) + ((f[4] + f[5]) + (f[6] + f[7]))) + f[8]
+    assert rho.dtype == np.float32
+    exact = math.fsum(rho.astype(np.float64).ravel())
+    d = sim.diagnostics()
+    assert abs(d[0] - exact) <= 1e-14 * exact, (d[0], exact)
+
+
+def lbm_ex(i):
+    return [0, 1, 0, -1, 0, 1, -1, -1, 1][i]
+
+
+def lbm_ey(i):
+    return [0, 0, 1, 0, -1, 1, 1, -1, -1][i]
 
 
 def test_wall_momentum_balance_on_gpu():
