@@ -112,6 +112,8 @@ template <class S>
 __global__ void __launch_bounds__(kRowThreads) k_adj1(KParams kp, AdjArgs aa)
 {
     typedef typename Codec<S>::R R;
+    grid_dependency_wait();
+    allow_dependent_launch();
     const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y;
     const int64_t node = (int64_t)y * kp.nx + x, k = (int64_t)y * kp.pitch + x;
     double gFx = 0.0, gFy = 0.0, gG = 0.0, gT = 0.0, Jt = 0.0;
@@ -304,6 +306,8 @@ template <class S>
 __global__ void __launch_bounds__(kRowThreads) k_adj2(KParams kp, AdjArgs aa)
 {
     typedef typename Codec<S>::R R;
+    grid_dependency_wait();
+    allow_dependent_launch();
     const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y;
     const int64_t node = (int64_t)y * kp.nx + x, k = (int64_t)y * kp.pitch + x;
     double gG = 0.0, gT = 0.0;
@@ -381,13 +385,11 @@ template <class S>
 struct Adjoint {
     static cudaError_t pass1(const KParams &kp, const AdjArgs &aa, cudaStream_t st)
     {
-        k_adj1<S><<<row_grid(kp), kRowThreads, 0, st>>>(kp, aa);
-        return cudaGetLastError();
+        return launch_dependent(k_adj1<S>, row_grid(kp), dim3(kRowThreads), 0, st, kp, aa);
     }
     static cudaError_t pass2(const KParams &kp, const AdjArgs &aa, cudaStream_t st)
     {
-        k_adj2<S><<<row_grid(kp), kRowThreads, 0, st>>>(kp, aa);
-        return cudaGetLastError();
+        return launch_dependent(k_adj2<S>, row_grid(kp), dim3(kRowThreads), 0, st, kp, aa);
     }
     static cudaError_t lambda(const KParams &kp, const AdjArgs &aa, double *out, cudaStream_t st)
     {

@@ -182,6 +182,10 @@ __global__ void __launch_bounds__(32 * (NW + 1)) k_fused(KParams kp, int seg_row
     const int first = yb - 2, last = ye + 1;  // staged rows
     const int x_lo = x0 - HX;
 
+    // the state this step reads is the one the previous step wrote, and this step writes
+    // the buffer the previous step read: nothing global is touched before it has completed
+    grid_dependency_wait();
+    allow_dependent_launch();
     if (threadIdx.x == 0) {
         for (int s = 0; s < RING; ++s) {
             mbar_init(full + s, 1);
@@ -349,8 +353,8 @@ struct Fused {
         if (nseg < 1) nseg = 1;
         const int seg_rows = (kp.ny + nseg - 1) / nseg;
         nseg = (kp.ny + seg_rows - 1) / seg_rows;
-        k_fused<S, NW, RING, P, O><<<dim3(strips, nseg), 32 * (NW + 1), L::bytes(kp.per_node_ref != 0), st>>>(kp, seg_rows);
-        return cudaGetLastError();
+        return launch_dependent(k_fused<S, NW, RING, P, O>, dim3(strips, nseg), dim3(32 * (NW + 1)),
+                                L::bytes(kp.per_node_ref != 0), st, kp, seg_rows);
     }
     // Fully periodic lattices with a constant force and one relaxation time get
     // instantiations with those options fixed at compile time; everything else reads them

@@ -40,6 +40,8 @@ template <class S>
 __global__ void __launch_bounds__(kRowThreads) k_psi(KParams kp)
 {
     typedef typename Codec<S>::R R;
+    grid_dependency_wait();
+    allow_dependent_launch();
     const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y;
     if (x >= kp.nx) return;
     const int64_t node = (int64_t)y * kp.nx + x;
@@ -58,6 +60,8 @@ template <class S>
 __global__ void __launch_bounds__(kRowThreads) k_collide(KParams kp)
 {
     typedef typename Codec<S>::R R;
+    grid_dependency_wait();
+    allow_dependent_launch();
     const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y;
     if (x >= kp.nx) return;
     const int64_t node = (int64_t)y * kp.nx + x;
@@ -244,13 +248,11 @@ template <class S>
 struct TwoPass {
     static cudaError_t psi_pass(const KParams &kp, cudaStream_t st)
     {
-        k_psi<S><<<row_grid(kp), kRowThreads, 0, st>>>(kp);
-        return cudaGetLastError();
+        return launch_dependent(k_psi<S>, row_grid(kp), dim3(kRowThreads), 0, st, kp);
     }
     static cudaError_t collide_pass(const KParams &kp, cudaStream_t st)
     {
-        k_collide<S><<<row_grid(kp), kRowThreads, 0, st>>>(kp);
-        return cudaGetLastError();
+        return launch_dependent(k_collide<S>, row_grid(kp), dim3(kRowThreads), 0, st, kp);
     }
     static cudaError_t init(const KParams &kp, const double *r, const double *u, const double *v, cudaStream_t st)
     {
@@ -269,7 +271,7 @@ struct TwoPass {
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         const int64_t n = (int64_t)kp.nx * kp.ny;
         int64_t blocks = (n + kRowThreads - 1) / kRowThreads;
-        if (blocks > 8 * (int64_t)sms) blocks = 8 * (int64_t)sms;
+        if (blocks > 32 * (int64_t)sms) blocks = 32 * (int64_t)sms;
         k_diag<S><<<(unsigned)blocks, kRowThreads, 0, st>>>(kp, acc, umax, nanc);
         return cudaGetLastError();
     }

@@ -31,6 +31,31 @@ __host__ __device__ constexpr R omega_(int i) { return i == 0 ? R(0) : (i <= 4 ?
 
 namespace lbm {
 
+// ------------------------------------------------ dependent launches ------
+// Kernels of the step chain are launched with programmatic stream serialization: the next
+// grid may be scheduled while the previous one drains, and waits here until that grid has
+// completed and its memory is visible, before touching global memory.  Launched without
+// that attribute, both instructions do nothing.
+__device__ __forceinline__ void grid_dependency_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void allow_dependent_launch() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
+template <class... KArgs, class... Args>
+inline cudaError_t launch_dependent(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                                    Args... args)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, args...);
+}
+
 template <class R>
 constexpr bool is_f64() { return std::is_same<R, double>::value; }
 
