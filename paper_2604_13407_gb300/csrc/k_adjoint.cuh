@@ -87,9 +87,14 @@ __device__ __forceinline__ void p_eos_derivs(const KParams &kp, R rho, R &p_rho,
     p_T = c.eos_K * rho * c.eos_R * g;
 }
 
-// Block sum of N per-thread doubles, added to acc[0..N-1] with one FP64 atomic each.
+// Per-block FP64 partial sums of the transposed passes (slots AdjSlot, lbm_internal.h):
+// one row of kAdjSlots doubles per block of the row grid, accumulated over all steps of a
+// call and reduced once at its end, so no atomic is contended and the summation order is
+// fixed.
+
+// Block sum of N per-thread doubles added to this block's slots [first, first + N).
 template <int N>
-__device__ __forceinline__ void block_add(const double (&v)[N], double *acc)
+__device__ __forceinline__ void block_add(const double (&v)[N], double *part, int first)
 {
     __shared__ double red[kRowThreads / 32][N];
     double w[N];
@@ -103,7 +108,22 @@ __device__ __forceinline__ void block_add(const double (&v)[N], double *acc)
     if (threadIdx.x < N) {
         double s = 0.0;
         for (int q = 0; q < kRowThreads / 32; ++q) s += red[q][threadIdx.x];
-        if (s != 0.0) atomicAdd(acc + threadIdx.x, s);
+        part[((int64_t)blockIdx.y * gridDim.x + blockIdx.x) * kAdjSlots + first + threadIdx.x] += s;
+    }
+}
+
+// Block sum of one double added to *acc with one FP64 atomic per block.
+__device__ __forceinline__ void block_atomic_add(double v, double *acc)
+{
+    __shared__ double red[kRowThreads / 32];
+    v = warp_sum(v);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (lane == 0) red[wid] = v;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double s = 0.0;
+        for (int q = 0; q < kRowThreads / 32; ++q) s += red[q];
+        if (s != 0.0) atomicAdd(acc, s);
     }
 }
 
@@ -128,7 +148,7 @@ __global__ void __launch_bounds__(kRowThreads) k_adj1(KParams kp, AdjArgs aa)
         const R rho = density<R>(f);
         const R jx = ((f[1] - f[3]) + (f[5] - f[6])) + (f[8] - f[7]);
         const R jy = ((f[2] - f[4]) + (f[5] + f[6])) - (f[7] + f[8]);
-        if (aa.J != nullptr) {
+        if (aa.sum_J) {
             // <W, A_t> at this node from its pulled populations: a population stored at x that
             // the next streaming sends into a wall is pulled back by x itself as f_i with
             // x - e_i a wall; every other one is pulled by exactly one fluid node
@@ -292,13 +312,8 @@ __global__ void __launch_bounds__(kRowThreads) k_adj1(KParams kp, AdjArgs aa)
         static_cast<R *>(aa.dpsi)[k] = dpsi_loc;
         static_cast<R *>(aa.rho)[k] = rho;
     }
-    if (aa.J != nullptr) {
-        const double v[5] = {gFx, gFy, gG, gT, Jt};
-        block_add<5>(v, aa.grad);  // aa.J == aa.grad + 4
-    } else {
-        const double v[4] = {gFx, gFy, gG, gT};
-        block_add<4>(v, aa.grad);
-    }
+    const double v[5] = {gFx, gFy, gG, gT, Jt};
+    block_add<5>(v, aa.part, SLOT_FX);
 }
 
 // Pass 2: dJ/dpsi(x) from the stencils that read psi(x), then c(x) = psi'(rho) dJ/dpsi.
@@ -334,8 +349,8 @@ __global__ void __launch_bounds__(kRowThreads) k_adj2(KParams kp, AdjArgs aa)
         gT = double(p_T / Gpsi * dpsi);
         gG = double(-psi / (R(2) * cc.G) * dpsi);
     }
-    const double v[4] = {0.0, 0.0, gG, gT};
-    block_add<4>(v, aa.grad);
+    const double v[2] = {gG, gT};
+    block_add<2>(v, aa.part, SLOT_G2);
 }
 
 // lambda_0 = dJ/dA at the starting state (no objective weight at t = 0), FP64 [9][ny][nx].
@@ -377,8 +392,26 @@ __global__ void __launch_bounds__(kRowThreads) k_objective(KParams kp, int objec
             if (w != 0.0) v += w * double(load_pop<S>(kp, i, x, y));
         }
     }
-    const double vv[1] = {v};
-    block_add<1>(vv, acc);
+    block_atomic_add(v, acc);
+}
+
+// Sum of the per-block slots: out[k] = sum over blocks of part[b][k], one block per slot,
+// in a fixed order (instantiated per storage type S, like the passes it sums).
+template <class S>
+__global__ void __launch_bounds__(256) k_adj_reduce(const double *part, int64_t blocks, double *out)
+{
+    __shared__ double red[8];
+    const int k = blockIdx.x;
+    double s = 0.0;
+    for (int64_t b = threadIdx.x; b < blocks; b += blockDim.x) s += part[b * kAdjSlots + k];
+    s = warp_sum(s);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int q = 0; q < 8; ++q) t += red[q];
+        out[k] = t;
+    }
 }
 
 template <class S>
@@ -394,6 +427,13 @@ struct Adjoint {
     static cudaError_t lambda(const KParams &kp, const AdjArgs &aa, double *out, cudaStream_t st)
     {
         k_adj_lambda<S><<<row_grid(kp), kRowThreads, 0, st>>>(kp, aa, out);
+        return cudaGetLastError();
+    }
+    // blocks of the row grid of the transposed passes (rows of the partial-sum array)
+    static int64_t blocks(const KParams &kp) { return (int64_t)row_grid(kp).x * row_grid(kp).y; }
+    static cudaError_t reduce(const KParams &kp, const double *part, double *out, cudaStream_t st)
+    {
+        k_adj_reduce<S><<<kAdjSlots, 256, 0, st>>>(part, blocks(kp), out);
         return cudaGetLastError();
     }
     static cudaError_t objective(const KParams &kp, int obj, double inv_nfluid, double *acc, cudaStream_t st)

@@ -46,6 +46,8 @@ Launchers launchers_f32()
     L.adj_pass2 = &Adjoint<float>::pass2;
     L.adj_lambda = &Adjoint<float>::lambda;
     L.objective = &Adjoint<float>::objective;
+    L.adj_blocks = &Adjoint<float>::blocks;
+    L.adj_reduce = &Adjoint<float>::reduce;
     L.fused_align = FusedGeom<float>::HX;
     return L;
 }

@@ -28,6 +28,8 @@ Launchers launchers_f64()
     L.adj_pass2 = &Adjoint<double>::pass2;
     L.adj_lambda = &Adjoint<double>::lambda;
     L.objective = &Adjoint<double>::objective;
+    L.adj_blocks = &Adjoint<double>::blocks;
+    L.adj_reduce = &Adjoint<double>::reduce;
     L.fused_tile_x = FusedLayout<double, LBM_FUSED_NW, LBM_FUSED_RING>::TX;
     L.fused_align = FusedGeom<double>::HX;
     return L;

@@ -61,10 +61,13 @@ struct Carver {
 struct Layout {
     std::vector<void *> ckpt, seg[2], psi[2];  // two sets of segment states and psi fields
     void *g[2], *c[2], *dS, *dpsi, *rho;
+    double *part;  // per-block partial sums of the transposed passes [blocks][kAdjSlots]
+    double *red;   // their column sums (kAdjSlots)
     double *acc;
 };
 
-size_t carve(Carver &cv, Layout &L, int64_t nseg, int64_t K, size_t state_bytes, size_t plane_r, size_t psi_bytes)
+size_t carve(Carver &cv, Layout &L, int64_t nseg, int64_t K, size_t state_bytes, size_t plane_r, size_t psi_bytes,
+             size_t part_bytes)
 {
     L.ckpt.resize(nseg);
     for (auto &b : L.ckpt) b = cv.take(state_bytes);
@@ -81,6 +84,8 @@ size_t carve(Carver &cv, Layout &L, int64_t nseg, int64_t K, size_t state_bytes,
     L.dS = cv.take(2 * plane_r);
     L.dpsi = cv.take(plane_r);
     L.rho = cv.take(plane_r);
+    L.part = static_cast<double *>(cv.take(part_bytes));
+    L.red = static_cast<double *>(cv.take(kAdjSlots * sizeof(double)));
     L.acc = static_cast<double *>(cv.take(8 * sizeof(double)));
     return cv.used;
 }
@@ -128,6 +133,7 @@ lbm_status adjoint_run(lbm_ctx *ctx, int64_t nsteps, int32_t K, int32_t objectiv
     const size_t real = v.elem;  // arithmetic type = storage type for FP64 and FP32
     const size_t plane_r = (size_t)v.plane * real;
     const size_t psi_bytes = (size_t)p.nx * p.ny * real;
+    const size_t part_bytes = (size_t)v.L->adj_blocks(*v.kp) * kAdjSlots * sizeof(double);
 
     // grad == NULL and lambda0 == NULL: the objective alone (forward sweep only)
     const bool backward = grad != nullptr || lambda0 != nullptr;
@@ -135,8 +141,8 @@ lbm_status adjoint_run(lbm_ctx *ctx, int64_t nsteps, int32_t K, int32_t objectiv
     // device memory, kept across calls
     Layout L;
     Carver probe{nullptr};
-    const size_t need = backward ? carve(probe, L, nseg, Kseg, state_bytes, plane_r, psi_bytes)
-                                 : carve(probe, L, 0, 1, 0, 0, 0);
+    const size_t need = backward ? carve(probe, L, nseg, Kseg, state_bytes, plane_r, psi_bytes, part_bytes)
+                                 : carve(probe, L, 0, 1, 0, 0, 0, 0);
     AdjointState *&as = *v.adj;
     if (!as) as = new AdjointState();
     if (as->bytes < need) {
@@ -156,8 +162,8 @@ lbm_status adjoint_run(lbm_ctx *ctx, int64_t nsteps, int32_t K, int32_t objectiv
         as->bytes = need;
     }
     Carver cv{static_cast<char *>(as->base)};
-    if (backward) carve(cv, L, nseg, Kseg, state_bytes, plane_r, psi_bytes);
-    else carve(cv, L, 0, 1, 0, 0, 0);
+    if (backward) carve(cv, L, nseg, Kseg, state_bytes, plane_r, psi_bytes, part_bytes);
+    else carve(cv, L, 0, 1, 0, 0, 0, 0);
     if (backward && !as->side) {
         ACK(cudaStreamCreateWithFlags(&as->side, cudaStreamNonBlocking), "cudaStreamCreate");
         cudaEvent_t *evs[] = {&as->fork, &as->recomputed[0], &as->recomputed[1], &as->reversed[0], &as->reversed[1]};
@@ -167,6 +173,7 @@ lbm_status adjoint_run(lbm_ctx *ctx, int64_t nsteps, int32_t K, int32_t objectiv
     const double inv_nfluid = 1.0 / double(v.n_fluid);
     const double w = 1.0 / double(nsteps);
     ACK(cudaMemsetAsync(L.acc, 0, 8 * sizeof(double), st), "memset");
+    if (backward) ACK(cudaMemsetAsync(L.part, 0, part_bytes, st), "memset");
 
     // ---- forward sweep: checkpoints and the objective
     KParams kq = *v.kp;
@@ -200,7 +207,7 @@ lbm_status adjoint_run(lbm_ctx *ctx, int64_t nsteps, int32_t K, int32_t objectiv
     aa.w_scale = w;
     aa.objective = objective;
     aa.inv_nfluid = inv_nfluid;
-    aa.grad = L.acc + 1;
+    aa.part = L.part;
     aa.dS = L.dS;
     aa.dpsi = L.dpsi;
     aa.rho = L.rho;
@@ -243,7 +250,7 @@ lbm_status adjoint_run(lbm_ctx *ctx, int64_t nsteps, int32_t K, int32_t objectiv
             aa.c_in = have_next ? L.c[gi] : nullptr;
             aa.g_out = L.g[gi ^ 1];
             aa.c_out = L.c[gi ^ 1];
-            aa.J = t >= 1 ? L.acc + 5 : nullptr;  // pass 1 adds <W, A_t> at grad + 4 = acc + 5
+            aa.sum_J = t >= 1;  // <W, A_0> is not part of J
             ACK(v.L->adj_pass1(kp, aa, st), "adjoint pass 1");
             ACK(v.L->adj_pass2(kp, aa, st), "adjoint pass 2");
             gi ^= 1;
@@ -265,12 +272,18 @@ lbm_status adjoint_run(lbm_ctx *ctx, int64_t nsteps, int32_t K, int32_t objectiv
         cudaFree(dl);
         ACK(e, "lambda0");
     }
-    double h[8];
+    ACK(v.L->adj_reduce(*v.kp, L.part, L.red, st), "adjoint reduction");
+    double h[8], r[kAdjSlots];
     ACK(cudaMemcpyAsync(h, L.acc, sizeof h, cudaMemcpyDeviceToHost, st), "D2H");
+    ACK(cudaMemcpyAsync(r, L.red, sizeof r, cudaMemcpyDeviceToHost, st), "D2H");
     ACK(cudaStreamSynchronize(st), "adjoint");
-    *J = (h[0] + h[5]) * w;
-    if (grad)
-        for (int k = 0; k < 4; ++k) grad[k] = h[1 + k];
+    *J = (h[0] + r[SLOT_J]) * w;
+    if (grad) {
+        grad[0] = r[SLOT_FX];
+        grad[1] = r[SLOT_FY];
+        grad[2] = r[SLOT_G1] + r[SLOT_G2];
+        grad[3] = r[SLOT_T1] + r[SLOT_T2];
+    }
     return v.check_error(ctx, msg);
 }
 

@@ -74,6 +74,12 @@ struct KParams {
     unsigned short inv_scale_bits;  // 2^-k in the storage type (FP16 or BF16 bits)
 };
 
+// Per-block partial sums of the transposed passes: slots of one row (8 doubles).  Pass 1:
+// dJ/dFx, dJ/dFy, dJ/dG (explicit and wall psi), dJ/dT (wall psi), <W, A_t>; pass 2:
+// dJ/dG and dJ/dT through psi(rho).
+constexpr int kAdjSlots = 8;
+enum AdjSlot { SLOT_FX = 0, SLOT_FY = 1, SLOT_G1 = 2, SLOT_T1 = 3, SLOT_J = 4, SLOT_G2 = 5, SLOT_T2 = 6 };
+
 // Buffers and scalars of one transposed step.  Planes use the population row pitch.
 struct AdjArgs {
     const void *g_in;   // [9] planes, g of the step after (null: lambda_{t+1} = W_{t+1} only)
@@ -86,8 +92,8 @@ struct AdjArgs {
     double w_scale;     // weight of W in lambda_{t+1} (1/n for J = (1/n) sum_t <W, A_t>)
     int objective;      // 0: y momentum handed to the walls by the next streaming; 1: mean j_x
     double inv_nfluid;  // 1 / number of fluid nodes (objective 1)
-    double *grad;       // FP64 accumulators: dJ/dFx, dJ/dFy, dJ/dG, dJ/dT
-    double *J;          // FP64 accumulator of <W, A_t> for the state of pass 1 (null: not summed)
+    double *part;       // per-block FP64 partial sums [blocks][kAdjSlots]
+    int sum_J;          // pass 1 also sums <W, A_t> of its state
 };
 
 // Storage precisions (match lbm_precision)
@@ -114,6 +120,8 @@ struct Launchers {
     cudaError_t (*adj_pass2)(const KParams &, const AdjArgs &, cudaStream_t);
     cudaError_t (*adj_lambda)(const KParams &, const AdjArgs &, double *out, cudaStream_t);
     cudaError_t (*objective)(const KParams &, int objective, double inv_nfluid, double *acc, cudaStream_t);
+    int64_t (*adj_blocks)(const KParams &);  // rows of the per-block partial-sum array (8 doubles each)
+    cudaError_t (*adj_reduce)(const KParams &, const double *part, double *out8, cudaStream_t);
     // fused kernel launch constraints
     int fused_tile_x;     // strip width in nodes
     int fused_align;      // nx must be a multiple of this
