@@ -39,17 +39,19 @@ __device__ __forceinline__ bool wall_link(const KParams &kp, int x, int y, int i
     return false;
 }
 
-// Objective weights W_i(x) at a fluid node (before the 1/n of the time average).
+// Objective weights W_i(x) at a fluid node (before the 1/n of the time average);
+// inv_nf = 1 / number of fluid nodes in the arithmetic type.
 template <class R>
-__device__ __forceinline__ R objective_weight(const AdjArgs &aa, int i, bool wall_ahead)
+__device__ __forceinline__ R objective_weight(int objective, int i, bool wall_ahead, R inv_nf)
 {
-    if (aa.objective == 0) return wall_ahead ? R(2 * ey_(i)) : R(0);
-    return R(ex_(i)) * R(aa.inv_nfluid);
+    if (objective == 0) return wall_ahead ? R(2 * ey_(i)) : R(0);
+    return R(ex_(i)) * inv_nf;
 }
 
 // lambda_{t+1} of the nine populations of fluid node (x, y).
 template <class R>
-__device__ __forceinline__ void lambda_at(const KParams &kp, const AdjArgs &aa, int x, int y, R wscale, R (&lam)[9])
+__device__ __forceinline__ void lambda_at(const KParams &kp, const AdjArgs &aa, int x, int y, R wscale, R inv_nf,
+                                          R (&lam)[9])
 {
     const int64_t k = (int64_t)y * kp.pitch + x;
     const R *g = static_cast<const R *>(aa.g_in);
@@ -58,7 +60,7 @@ __device__ __forceinline__ void lambda_at(const KParams &kp, const AdjArgs &aa, 
     for (int i = 0; i < 9; ++i) {
         int64_t kn = k;
         const bool wall = (i != 0) && wall_link(kp, x, y, i, kn);
-        R v = wscale * objective_weight<R>(aa, i, wall);
+        R v = wscale * objective_weight<R>(aa.objective, i, wall, inv_nf);
         if (g != nullptr) {
             if (wall) v += g[opp_(i) * kp.plane + k] + c[k];
             else v += g[i * kp.plane + kn] + c[kn];
@@ -92,23 +94,41 @@ __device__ __forceinline__ void p_eos_derivs(const KParams &kp, R rho, R &p_rho,
 // call and reduced once at its end, so no atomic is contended and the summation order is
 // fixed.
 
-// Block sum of N per-thread doubles added to this block's slots [first, first + N).
-template <int N>
-__device__ __forceinline__ void block_add(const double (&v)[N], double *part, int first)
+// Warp sum of one value per lane, returned as a double.  FP64 arithmetic sums in FP64;
+// FP32 arithmetic sums compensated pairs (Knuth's TwoSum at every shuffle level, about
+// 2^-48 relative) and converts once, which keeps FP64 work (a narrow pipe on GB300) out of
+// the per-node path.
+__device__ __forceinline__ double warp_sum_r(double v) { return warp_sum(v); }
+__device__ __forceinline__ double warp_sum_r(float v)
+{
+    float hi = v, lo = 0.f;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const float ohi = __shfl_down_sync(0xffffffffu, hi, o), olo = __shfl_down_sync(0xffffffffu, lo, o);
+        const float sum = hi + ohi, z = sum - hi;
+        lo += olo + ((hi - (sum - z)) + (ohi - z));
+        hi = sum;
+    }
+    return double(hi) + double(lo);
+}
+
+// Block sum of N per-thread values added to this block's slots [first, first + N).
+template <int N, class R>
+__device__ __forceinline__ void block_add(const R (&v)[N], double *part, int first)
 {
     __shared__ double red[kRowThreads / 32][N];
     double w[N];
 #pragma unroll
-    for (int k = 0; k < N; ++k) w[k] = warp_sum(v[k]);
+    for (int k = 0; k < N; ++k) w[k] = warp_sum_r(v[k]);
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     if (lane == 0)
 #pragma unroll
         for (int k = 0; k < N; ++k) red[wid][k] = w[k];
     __syncthreads();
     if (threadIdx.x < N) {
-        double s = 0.0;
-        for (int q = 0; q < kRowThreads / 32; ++q) s += red[q][threadIdx.x];
-        part[((int64_t)blockIdx.y * gridDim.x + blockIdx.x) * kAdjSlots + first + threadIdx.x] += s;
+        double t = 0.0;
+        for (int q = 0; q < kRowThreads / 32; ++q) t += red[q][threadIdx.x];
+        part[((int64_t)blockIdx.y * gridDim.x + blockIdx.x) * kAdjSlots + first + threadIdx.x] += t;
     }
 }
 
@@ -136,11 +156,12 @@ __global__ void __launch_bounds__(kRowThreads) k_adj1(KParams kp, AdjArgs aa)
     allow_dependent_launch();
     const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y;
     const int64_t node = (int64_t)y * kp.nx + x, k = (int64_t)y * kp.pitch + x;
-    double gFx = 0.0, gFy = 0.0, gG = 0.0, gT = 0.0, Jt = 0.0;
+    R gFx = R(0), gFy = R(0), gG = R(0), gT = R(0), Jt = R(0);
+    const R inv_nf = R(aa.inv_nfluid);
     if (x < kp.nx && !node_is_solid(kp, node)) {
         const Consts<R> &cc = cst<R>(kp);
         R lam[9];
-        lambda_at<R>(kp, aa, x, y, R(aa.w_scale), lam);
+        lambda_at<R>(kp, aa, x, y, R(aa.w_scale), inv_nf, lam);
 
         // ---- forward quantities at this node
         R f[9];
@@ -162,7 +183,7 @@ __global__ void __launch_bounds__(kRowThreads) k_adj1(KParams kp, AdjArgs aa)
                     wall_y += R(ey_(i)) * f[i];
                 }
             }
-            Jt = aa.objective == 0 ? double(R(-2) * wall_y) : double(jx - R(2) * wall_x) * aa.inv_nfluid;
+            Jt = aa.objective == 0 ? R(-2) * wall_y : (jx - R(2) * wall_x) * inv_nf;
         }
         const R *psif = static_cast<const R *>(kp.psi);
         const R psi = psif[node];
@@ -267,11 +288,11 @@ __global__ void __launch_bounds__(kRowThreads) k_adj1(KParams kp, AdjArgs aa)
         drho -= (ux * dux + uy * duy) * inv;
         // F = -G psi S + F_ext
         if (kp.force_mode == 0) {
-            gFx = double(dFx);
-            gFy = double(dFy);
+            gFx = dFx;
+            gFy = dFy;
         } else {
-            gFx = double((rho - cc.rho_g) * dFx);
-            gFy = double((rho - cc.rho_g) * dFy);
+            gFx = (rho - cc.rho_g) * dFx;
+            gFy = (rho - cc.rho_g) * dFy;
             drho += cc.Fx * dFx + cc.Fy * dFy;
         }
         const R dpsi_loc = -G * (Sx * dFx + Sy * dFy);
@@ -287,11 +308,11 @@ __global__ void __launch_bounds__(kRowThreads) k_adj1(KParams kp, AdjArgs aa)
         }
         if (dpsi_s != R(0)) {
             R prs, pTs;
-            p_eos_derivs<R>(kp, R(kp.rho_s), prs, pTs);
+            p_eos_derivs<R>(kp, cc.rho_s, prs, pTs);
             dG += -cc.psi_s / (R(2) * G) * dpsi_s;
-            gT = double(pTs / (G * cc.psi_s) * dpsi_s);
+            gT = pTs / (G * cc.psi_s) * dpsi_s;
         }
-        gG = double(dG);
+        gG = dG;
 
         // g_i = drho + e_i . dj + (M^T dm)_i
         const R base_ax = -dm1 - R(2) * dm2, base_dg = R(2) * dm1 + dm2;
@@ -312,7 +333,7 @@ __global__ void __launch_bounds__(kRowThreads) k_adj1(KParams kp, AdjArgs aa)
         static_cast<R *>(aa.dpsi)[k] = dpsi_loc;
         static_cast<R *>(aa.rho)[k] = rho;
     }
-    const double v[5] = {gFx, gFy, gG, gT, Jt};
+    const R v[5] = {gFx, gFy, gG, gT, Jt};
     block_add<5>(v, aa.part, SLOT_FX);
 }
 
@@ -325,7 +346,7 @@ __global__ void __launch_bounds__(kRowThreads) k_adj2(KParams kp, AdjArgs aa)
     allow_dependent_launch();
     const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y;
     const int64_t node = (int64_t)y * kp.nx + x, k = (int64_t)y * kp.pitch + x;
-    double gG = 0.0, gT = 0.0;
+    R gG = R(0), gT = R(0);
     if (x < kp.nx && !node_is_solid(kp, node)) {
         const Consts<R> &cc = cst<R>(kp);
         const R *dS = static_cast<const R *>(aa.dS);
@@ -346,10 +367,10 @@ __global__ void __launch_bounds__(kRowThreads) k_adj2(KParams kp, AdjArgs aa)
         // psi^2 = 2 (p - rho/3)/G
         const R Gpsi = cc.G * psi;
         static_cast<R *>(aa.c_out)[k] = (p_rho - R(1.0 / 3.0)) / Gpsi * dpsi;
-        gT = double(p_T / Gpsi * dpsi);
-        gG = double(-psi / (R(2) * cc.G) * dpsi);
+        gT = p_T / Gpsi * dpsi;
+        gG = -psi / (R(2) * cc.G) * dpsi;
     }
-    const double v[2] = {gG, gT};
+    const R v[2] = {gG, gT};
     block_add<2>(v, aa.part, SLOT_G2);
 }
 
@@ -366,7 +387,7 @@ __global__ void __launch_bounds__(kRowThreads) k_adj_lambda(KParams kp, AdjArgs 
 #pragma unroll
         for (int i = 0; i < 9; ++i) lam[i] = R(0);
     } else {
-        lambda_at<R>(kp, aa, x, y, R(0), lam);
+        lambda_at<R>(kp, aa, x, y, R(0), R(aa.inv_nfluid), lam);
     }
 #pragma unroll
     for (int i = 0; i < 9; ++i) out[i * n + node] = double(lam[i]);
@@ -388,7 +409,7 @@ __global__ void __launch_bounds__(kRowThreads) k_objective(KParams kp, int objec
         for (int i = 0; i < 9; ++i) {
             int64_t kn;
             const bool wall = (i != 0) && wall_link(kp, x, y, i, kn);
-            const double w = double(objective_weight<R>(aa, i, wall));
+            const double w = double(objective_weight<R>(aa.objective, i, wall, R(aa.inv_nfluid)));
             if (w != 0.0) v += w * double(load_pop<S>(kp, i, x, y));
         }
     }

@@ -193,7 +193,7 @@ static void fill_constants(lbm_ctx *c)
     LBM_FILL(eos_a) LBM_FILL(eos_b) LBM_FILL(eos_RT) LBM_FILL(eos_R) LBM_FILL(eos_K) LBM_FILL(two_over_G) LBM_FILL(G)
     LBM_FILL(kq1) LBM_FILL(kq7) LBM_FILL(c1G) LBM_FILL(c2G) LBM_FILL(q2fac) LBM_FILL(sp) LBM_FILL(sq)
     LBM_FILL(nu_l) LBM_FILL(nu_g) LBM_FILL(rho_l) LBM_FILL(rho_g) LBM_FILL(Lambda) LBM_FILL(Fx) LBM_FILL(Fy)
-    LBM_FILL(psi_s) LBM_FILL(rho_ref) LBM_FILL(scale) LBM_FILL(inv_scale)
+    LBM_FILL(psi_s) LBM_FILL(rho_s) LBM_FILL(rho_ref) LBM_FILL(scale) LBM_FILL(inv_scale)
 #undef LBM_FILL
     k.cd.hsp = 1.0 - 0.5 * k.sp;
     k.cd.hsq = 1.0 - 0.5 * k.sq;

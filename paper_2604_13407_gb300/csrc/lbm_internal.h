@@ -10,7 +10,7 @@ namespace lbm {
 // no kernel converts between double and float per node (GB300's FP64 pipe is narrow).
 template <class R>
 struct Consts {
-    R eos_a, eos_b, eos_RT, eos_R, eos_K, two_over_G, G, kq1, kq7, c1G, c2G, q2fac, sp, sq, nu_l, nu_g, rho_l, rho_g, Lambda, Fx, Fy, psi_s, rho_ref, scale, inv_scale;
+    R eos_a, eos_b, eos_RT, eos_R, eos_K, two_over_G, G, kq1, kq7, c1G, c2G, q2fac, sp, sq, nu_l, nu_g, rho_l, rho_g, Lambda, Fx, Fy, psi_s, rho_s, rho_ref, scale, inv_scale;
     R hsp, hsq;  // 1 - s_p/2 and 1 - s_q/2 of the constant relaxation rates
 };
 
