@@ -83,7 +83,8 @@ def test_checkpoint_interval_does_not_change_the_result(references):
         J, g, lam = gpu_sim(p, solid, lbm.F64, A0).adjoint(12, K, lbm.OBJ_WALL_FORCE_Y, want_lambda0=True)
         res.append((J, g, lam))
     for J, g, lam in res[1:]:
-        # J and the gradients are FP64 sums whose block order is not fixed (atomics)
+        # the gradients are summed in a fixed order; J includes one FP64 sum whose block
+        # order is not fixed (the objective of the last state, added with atomics)
         assert abs(J - res[0][0]) <= 1e-14 * abs(res[0][0])
         assert np.abs(g - res[0][1]).max() <= 1e-13 * np.abs(res[0][1]).max()
         assert np.array_equal(lam, res[0][2])
