@@ -1,0 +1,238 @@
+"""Two-phase Poiseuille flow of Sec. 3.1 (Table 1), with half-way bounce-back walls in place
+of the paper's wall scheme.
+
+Set-up (Sec. 3.1): van der Waals EOS (a = 9/49, b = 2/21, R = 1, K_EOS = 1/16); walls a
+distance W = 128 sqrt 2 apart; gas layers of W/4 at the walls, liquid layer of W/2 in the
+middle; driving force |F| = 2e-7 along the walls; (epsilon, T_r) = (0, 0.72), (1, 0.65),
+(2, 0.54); tau = 0.8 and 1.5; k1 = k2 = -epsilon/16; Lambda = 1/12.
+
+* grid-aligned: a column of 181 nodes (W = 181, the integer nearest 128 sqrt 2), periodic
+  along the walls, half-way walls at y = -1/2 and 180.5; the GPU runs it 4 nodes wide;
+* grid-oblique: a periodic 256 x 256 lattice with two-node solid bands where
+  (x - y) mod 256 is 0 or 1 (W = 254 / sqrt 2 = 179.6 between the bands' inner faces),
+  force along (1, 1)/sqrt 2, profile along alpha = x - y.
+
+Each run goes to the steady state the paper's analysis assumes.  The heavy liquid layer moves
+almost as a plug held back by the thin gas layers, so the flow relaxes over many viscous
+times W^2 / nu.  The interfaces are first equilibrated without force; the run then restarts
+from that density with the Eq. (u.plane) velocity of it and steps until the velocity changes
+by less than 1e-7 (relative) over a quarter viscous time (converge() below).  All runs are
+FP64.  Err is Sec. 3.1's relative error of the velocity along the walls against
+Eq. (u.plane) integrated with the converged density profile.
+
+The driver takes a backend: the GPU library (`python -m tests.table1 [--quick]`, JSON lines)
+or the CPU oracle (tests/golden/make_table1_oracle.py, aligned rows only).
+"""
+import argparse
+import json
+import math
+import pathlib
+import sys
+import time
+
+import numpy as np
+
+from oracle import analytic as A
+from paper_2604_13407_gb300 import inputs as I
+from tests.setups import vdw_case, vdw_params
+
+CASES = ((0.0, 0.72), (1.0, 0.65), (2.0, 0.54))
+TAUS = (0.8, 1.5)
+F_DRIVE = 2e-7
+WIDTH_ALIGNED = 181
+N_OBLIQUE = 256
+EQUILIBRATION_STEPS = 20000
+TOL = 1e-7
+
+# Table 1 as printed (Err x 100): "epsilon geometry" -> original tau 0.8, original tau 1.5,
+# improved tau 0.8, improved tau 1.5
+PAPER = json.loads((pathlib.Path(__file__).parent / "golden" / "table1_paper.json").read_text())["rows"]
+
+
+def paper_err(eps, geometry, tau, scheme):
+    return 1e-2 * PAPER["%d %s" % (eps, geometry)][2 * scheme + TAUS.index(tau)]
+
+
+def converge(sim, chunk, tol=TOL, max_chunks=400):
+    """Step in chunks until max |du| / max |u| over a chunk is below tol; returns the last
+    change and the steps taken.
+
+    After every chunk the run restarts from the average of two consecutive states (the
+    scheme keeps an undamped period-2 mode).  Near the steady state the slowest mode, the
+    liquid plug sliding on the gas layers, decays by a fixed ratio r per chunk; once three
+    successive chunk states show the same r (to 1 %), the state is extrapolated to the
+    limit, S + dS r / (1 - r) (Aitken's delta-squared on the whole state), which removes that
+    mode and cuts the chunks needed about threefold."""
+    prev_u, change, steps = None, None, 0
+    hist, r_prev = [], None
+    for _ in range(max_chunks):
+        sim.step(chunk)
+        a0 = sim.get_state()
+        sim.step(1)
+        S = 0.5 * (a0 + sim.get_state())
+        sim.set_state(S)
+        steps += chunk + 1
+        _, u, v = sim.moments()
+        if prev_u is not None:
+            change = max(np.abs(u - prev_u[0]).max(), np.abs(v - prev_u[1]).max()) / max(np.abs(u).max(), np.abs(v).max())
+            if change < tol:
+                break
+        prev_u = (u, v)
+        if len(hist) >= 2:
+            dS, dP = S - hist[-1], hist[-1] - hist[-2]
+            r = float((dS * dP).sum() / (dP * dP).sum())
+            if r_prev is not None and 0.0 < r < 0.999 and abs(r - r_prev) < 0.01 * r:
+                S = S + dS * (r / (1.0 - r))
+                sim.set_state(S)
+                hist, r_prev, prev_u = [], None, None
+            else:
+                r_prev = r
+        hist = hist[-1:] + [S]
+    return change, steps
+
+
+def nu_fn(p):
+    return lambda r: A.nu_of_rho(r, p.tau_l, p.tau_g, p.rho_l, p.rho_g)
+
+
+def psi_real_limit(op, rho_from):
+    """Largest density above rho_from up to which psi = sqrt(2 (p - rho/3) / G) stays real
+    (G < 0: p_EOS < rho/3) for the van der Waals EOS, less 1 %; p diverges at 1/b."""
+    xs = np.linspace(rho_from, (1.0 - 1e-9) / op.b, 200001)
+    p = xs * op.R * op.T / (1.0 - op.b * xs) - op.a * xs * xs
+    bad = np.nonzero(p - xs / 3.0 >= 0.0)[0]
+    return 0.99 * (xs[bad[0]] if len(bad) else xs[-1])
+
+
+class GpuBackend:
+    """The GPU library in FP64; the aligned column runs 4 nodes wide."""
+    aligned_nx = 4
+
+    def __init__(self, precision=None):
+        from paper_2604_13407_gb300 import lbm
+        self.lbm = lbm
+        self.precision = lbm.F64 if precision is None else precision
+
+    def make(self, op, solid=None):
+        from tests import gpu_cases as GC
+        gp = GC.gpu_params(op, self.precision)
+        gp.rho_max = psi_real_limit(op, op.rho_l)
+        sim = self.lbm.Simulation(gp)
+        if solid is not None:
+            sim.set_geometry(solid)
+        return sim
+
+
+class _OracleRun:
+    def __init__(self, sim):
+        self.sim = sim
+
+    def init_fields(self, rho, ux=None, uy=None):
+        self.sim.init(rho, ux, uy)
+
+    def step(self, n):
+        self.sim.step(n)
+
+    def get_state(self):
+        return self.sim.get_state().copy()
+
+    def set_state(self, S):
+        self.sim.set_state(S)
+
+    def moments(self):
+        f = self.sim.fields()
+        return f["rho"], f["ux"], f["uy"]
+
+
+class OracleBackend:
+    """The FP64 CPU oracle; the aligned column runs 1 node wide."""
+    aligned_nx = 1
+
+    def make(self, op, solid=None):
+        from oracle import oracle as O
+        return _OracleRun(O.OracleSim(op, solid=solid))
+
+
+def run_aligned(backend, eps, t_r, tau, scheme, width=WIDTH_ALIGNED, tol=TOL):
+    """Grid-aligned channel: equilibrate the interfaces without force, restart from the
+    equilibrated density with the Eq. (u.plane) velocity of that density, converge.
+    Returns Err, the last relative change, the steps and the liquid-to-gas ratio."""
+    T, rg, rl = vdw_case(t_r)
+    nx = backend.aligned_nx
+    mk = lambda F: vdw_params(eps, t_r, nx=nx, ny=width, periodic_x=True, periodic_y=False, Fx=F,
+                              scheme=scheme, tau_l=tau, tau_g=tau)
+    sim = backend.make(mk(0.0))
+    sim.init_fields(I.tanh_slab(nx, width, rl, rg, width / 2.0))
+    sim.step(EQUILIBRATION_STEPS)
+    rho, _, _ = sim.moments()
+    op = mk(F_DRIVE)
+    u0 = A.poiseuille_theory(rho[:, 0], F_DRIVE, nu_fn(op))
+    sim = backend.make(op)
+    sim.init_fields(rho, np.repeat(u0[:, None], nx, axis=1), None)
+    nu = (tau - 0.5) / 3.0
+    change, steps = converge(sim, int(0.25 * width * width / nu), tol)
+    rho, ux, _ = sim.moments()
+    th = A.poiseuille_theory(rho[:, 0], F_DRIVE, nu_fn(op))
+    return A.err_norm(ux[:, 0], th), change, steps, float(rho[:, 0].max() / rho[:, 0].min())
+
+
+def run_oblique(backend, eps, t_r, tau, scheme, n=N_OBLIQUE, tol=TOL):
+    """Grid-oblique channel, same two stages; the profile is along alpha = x - y."""
+    T, rg, rl = vdw_case(t_r)
+    f = F_DRIVE / math.sqrt(2.0)
+    mk = lambda F: vdw_params(eps, t_r, nx=n, ny=n, periodic_x=True, periodic_y=True, Fx=F, Fy=F,
+                              scheme=scheme, tau_l=tau, tau_g=tau)
+    solid = I.oblique_band_walls(n)
+    sim = backend.make(mk(0.0), solid)
+    sim.init_fields(np.where(solid == 1, rg, I.oblique_slab(n, rl, rg, n // 2)))
+    sim.step(EQUILIBRATION_STEPS)
+    rho, _, _ = sim.moments()
+    op = mk(f)
+    idx = np.arange(2, n)  # fluid nodes (x = i, y = 0) along alpha
+    spacing = 1.0 / math.sqrt(2.0)
+    ub0 = np.zeros(n)
+    ub0[idx] = A.poiseuille_theory(rho[0, idx], F_DRIVE, nu_fn(op), spacing=spacing)
+    alpha = (np.arange(n)[None, :] - np.arange(n)[:, None]) % n
+    ub = ub0[alpha]
+    sim = backend.make(op, solid)
+    sim.init_fields(rho, ub / math.sqrt(2.0), ub / math.sqrt(2.0))
+    nu = (tau - 0.5) / 3.0
+    width = (n - 2) * spacing
+    change, steps = converge(sim, int(0.25 * width * width / nu), tol)
+    rho, ux, uy = sim.moments()
+    ubs = (ux[0, idx] + uy[0, idx]) / math.sqrt(2.0)
+    th = A.poiseuille_theory(rho[0, idx], F_DRIVE, nu_fn(op), spacing=spacing)
+    return A.err_norm(ubs, th), change, steps, float(rho[0, idx].max() / rho[0, idx].min())
+
+
+RUNNERS = {"aligned": run_aligned, "oblique": run_oblique}
+
+
+def record(backend, geometry, eps, t_r, tau, scheme):
+    t0 = time.time()
+    err, change, steps, ratio = RUNNERS[geometry](backend, eps, t_r, tau, scheme)
+    return {"case": geometry, "epsilon": eps, "T_r": t_r, "tau": tau,
+            "scheme": ["original", "improved"][scheme], "Err": err,
+            "paper_Err": paper_err(eps, geometry, tau, scheme), "density_ratio": ratio,
+            "last_chunk_change": change, "steps": steps, "seconds": round(time.time() - t0, 1)}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--quick", action="store_true", help="tau = 1.5 only")
+    ap.add_argument("--geometry", choices=("aligned", "oblique", "both"), default="both")
+    args = ap.parse_args()
+    import torch
+    torch.cuda.set_device(0)
+    backend = GpuBackend()
+    taus = (1.5,) if args.quick else TAUS
+    geoms = ("aligned", "oblique") if args.geometry == "both" else (args.geometry,)
+    for geom in geoms:
+        for eps, t_r in CASES:
+            for tau in taus:
+                for scheme in (0, 1):
+                    print(json.dumps(record(backend, geom, eps, t_r, tau, scheme)), flush=True)
+
+
+if __name__ == "__main__":
+    sys.exit(main())
