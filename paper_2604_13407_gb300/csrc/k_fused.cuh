@@ -348,7 +348,12 @@ struct Fused {
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         const int strips = (kp.nx + L::TX - 1) / L::TX;
         int nseg = (16 * sms + strips - 1) / strips;
-        const int max_seg = kp.ny / 16 > 0 ? kp.ny / 16 : 1;
+        // a CTA walks its segment row by row, so short segments cut the latency of small
+        // lattices; each segment re-reads 3 halo rows, which come from L2 while the two
+        // population buffers fit in it
+        const double state_bytes = 2.0 * 9.0 * (double)kp.plane * sizeof(S);
+        const int min_rows = state_bytes <= 64.0 * 1024 * 1024 ? 4 : 16;
+        const int max_seg = kp.ny / min_rows > 0 ? kp.ny / min_rows : 1;
         if (nseg > max_seg) nseg = max_seg;
         if (nseg < 1) nseg = 1;
         const int seg_rows = (kp.ny + nseg - 1) / nseg;

@@ -53,7 +53,7 @@ def paper_err(eps, geometry, tau, scheme):
     return 1e-2 * PAPER["%d %s" % (eps, geometry)][2 * scheme + TAUS.index(tau)]
 
 
-def converge(sim, chunk, tol=TOL, max_chunks=400):
+def converge(sim, chunk, tol=TOL, max_chunks=400, log=None):
     """Step in chunks until max |du| / max |u| over a chunk is below tol; returns the last
     change and the steps taken.
 
@@ -78,10 +78,14 @@ def converge(sim, chunk, tol=TOL, max_chunks=400):
             if change < tol:
                 break
         prev_u = (u, v)
+        if log is not None:
+            log(steps, change)
         if len(hist) >= 2:
             dS, dP = S - hist[-1], hist[-1] - hist[-2]
             r = float((dS * dP).sum() / (dP * dP).sum())
             if r_prev is not None and 0.0 < r < 0.999 and abs(r - r_prev) < 0.01 * r:
+                if log is not None:
+                    log(steps, "extrapolate r = %.4f" % r)
                 S = S + dS * (r / (1.0 - r))
                 sim.set_state(S)
                 hist, r_prev, prev_u = [], None, None
@@ -153,7 +157,7 @@ class OracleBackend:
         return _OracleRun(O.OracleSim(op, solid=solid))
 
 
-def run_aligned(backend, eps, t_r, tau, scheme, width=WIDTH_ALIGNED, tol=TOL):
+def run_aligned(backend, eps, t_r, tau, scheme, width=WIDTH_ALIGNED, tol=TOL, max_chunks=400, log=None):
     """Grid-aligned channel: equilibrate the interfaces without force, restart from the
     equilibrated density with the Eq. (u.plane) velocity of that density, converge.
     Returns Err, the last relative change, the steps and the liquid-to-gas ratio."""
@@ -170,13 +174,13 @@ def run_aligned(backend, eps, t_r, tau, scheme, width=WIDTH_ALIGNED, tol=TOL):
     sim = backend.make(op)
     sim.init_fields(rho, np.repeat(u0[:, None], nx, axis=1), None)
     nu = (tau - 0.5) / 3.0
-    change, steps = converge(sim, int(0.25 * width * width / nu), tol)
+    change, steps = converge(sim, int(0.25 * width * width / nu), tol, max_chunks, log=log)
     rho, ux, _ = sim.moments()
     th = A.poiseuille_theory(rho[:, 0], F_DRIVE, nu_fn(op))
     return A.err_norm(ux[:, 0], th), change, steps, float(rho[:, 0].max() / rho[:, 0].min())
 
 
-def run_oblique(backend, eps, t_r, tau, scheme, n=N_OBLIQUE, tol=TOL):
+def run_oblique(backend, eps, t_r, tau, scheme, n=N_OBLIQUE, tol=TOL, log=None, max_chunks=400):
     """Grid-oblique channel, same two stages; the profile is along alpha = x - y."""
     T, rg, rl = vdw_case(t_r)
     f = F_DRIVE / math.sqrt(2.0)
@@ -198,7 +202,7 @@ def run_oblique(backend, eps, t_r, tau, scheme, n=N_OBLIQUE, tol=TOL):
     sim.init_fields(rho, ub / math.sqrt(2.0), ub / math.sqrt(2.0))
     nu = (tau - 0.5) / 3.0
     width = (n - 2) * spacing
-    change, steps = converge(sim, int(0.25 * width * width / nu), tol)
+    change, steps = converge(sim, int(0.25 * width * width / nu), tol, max_chunks, log=log)
     rho, ux, uy = sim.moments()
     ubs = (ux[0, idx] + uy[0, idx]) / math.sqrt(2.0)
     th = A.poiseuille_theory(rho[0, idx], F_DRIVE, nu_fn(op), spacing=spacing)
@@ -208,30 +212,45 @@ def run_oblique(backend, eps, t_r, tau, scheme, n=N_OBLIQUE, tol=TOL):
 RUNNERS = {"aligned": run_aligned, "oblique": run_oblique}
 
 
-def record(backend, geometry, eps, t_r, tau, scheme):
+def record(backend, geometry, eps, t_r, tau, scheme, tol=TOL, max_chunks=400, log=None):
     t0 = time.time()
-    err, change, steps, ratio = RUNNERS[geometry](backend, eps, t_r, tau, scheme)
+    err, change, steps, ratio = RUNNERS[geometry](backend, eps, t_r, tau, scheme, tol=tol, max_chunks=max_chunks,
+                                                  log=log)
     return {"case": geometry, "epsilon": eps, "T_r": t_r, "tau": tau,
             "scheme": ["original", "improved"][scheme], "Err": err,
             "paper_Err": paper_err(eps, geometry, tau, scheme), "density_ratio": ratio,
-            "last_chunk_change": change, "steps": steps, "seconds": round(time.time() - t0, 1)}
+            "precision": getattr(backend, "name", "f64"), "tol": tol, "last_chunk_change": change, "steps": steps,
+            "seconds": round(time.time() - t0, 1),
+            "us_per_step": round(1e6 * (time.time() - t0) / (steps + EQUILIBRATION_STEPS), 2)}
 
 
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--quick", action="store_true", help="tau = 1.5 only")
     ap.add_argument("--geometry", choices=("aligned", "oblique", "both"), default="both")
+    ap.add_argument("--tol", type=float, default=TOL)
+    ap.add_argument("--max-chunks", type=int, default=400)
+    ap.add_argument("--precision", choices=("f64", "f32"), default="f64")
+    ap.add_argument("--scheme", type=int, nargs="*", default=[0, 1])
+    ap.add_argument("--eps", type=float, nargs="*", default=[c[0] for c in CASES])
+    ap.add_argument("--log", action="store_true", help="per-chunk change on stderr")
     args = ap.parse_args()
     import torch
     torch.cuda.set_device(0)
-    backend = GpuBackend()
+    from paper_2604_13407_gb300 import lbm
+    backend = GpuBackend({"f64": lbm.F64, "f32": lbm.F32}[args.precision])
+    backend.name = args.precision
     taus = (1.5,) if args.quick else TAUS
     geoms = ("aligned", "oblique") if args.geometry == "both" else (args.geometry,)
     for geom in geoms:
         for eps, t_r in CASES:
+            if eps not in args.eps:
+                continue
             for tau in taus:
-                for scheme in (0, 1):
-                    print(json.dumps(record(backend, geom, eps, t_r, tau, scheme)), flush=True)
+                for scheme in args.scheme:
+                    log = (lambda st, c: print(st, c, file=sys.stderr, flush=True)) if args.log else None
+                    print(json.dumps(record(backend, geom, eps, t_r, tau, scheme, args.tol, args.max_chunks, log)),
+                          flush=True)
 
 
 if __name__ == "__main__":
