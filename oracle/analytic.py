@@ -164,6 +164,26 @@ def poiseuille_theory(rho_nodes, F, nu_fn, spacing=1.0, sub=400):
     return np.interp(nodes, s, u)
 
 
+def annular_theory(r_nodes, rho_nodes, F_fn, nu_fn, R_i, R_o, sub=400):
+    """Integrate Eq. (u.annular), (1/r^2) d/dr [rho nu r^3 d(u/r)/dr] = -F(r), between
+    no-slip cylinders at r = R_i and R_o, with the density interpolated linearly between
+    the sampled radii r_nodes (held constant between the outermost samples and the walls).
+    With mu = rho nu and G(r) = int_{R_i}^r s^2 F(s) ds the first integral is
+    mu r^3 d(u/r)/dr = C - G(r), so u/r = int_{R_i}^r (C - G)/(mu s^3) ds, and C makes u vanish
+    at R_o.  Returns u at r_nodes."""
+    r_nodes = np.asarray(r_nodes, dtype=np.float64)
+    rho_nodes = np.asarray(rho_nodes, dtype=np.float64)
+    s = np.linspace(R_i, R_o, (len(r_nodes) + 1) * sub + 1)
+    rho_s = np.interp(s, r_nodes, rho_nodes)
+    mu = rho_s * nu_fn(rho_s)
+    G = integrate.cumulative_trapezoid(s * s * F_fn(s), s, initial=0.0)
+    i1 = integrate.trapezoid(1.0 / (mu * s**3), s)
+    iG = integrate.trapezoid(G / (mu * s**3), s)
+    C = iG / i1
+    w = integrate.cumulative_trapezoid((C - G) / (mu * s**3), s, initial=0.0)
+    return np.interp(r_nodes, s, s * w)
+
+
 def err_norm(u_sim, u_th):
     """Err of Sec. 3.1: sqrt(sum (u_sim - u_th)^2 / sum u_th^2)."""
     u_sim = np.asarray(u_sim)

@@ -1,0 +1,140 @@
+"""Two-phase annular shear flow of Sec. 3.2 on the GPU library, with interpolated
+(Bouzidi) bounce-back on the two cylinders in place of the paper's wall scheme.
+
+Set-up (Sec. 3.2): van der Waals EOS (a = 9/49, b = 2/21, R = 1, K_EOS = 1/16) at
+T_r = 0.5 (liquid-to-gas ratio about 113), epsilon = 1.895, tau = 0.8, Lambda = 1/12;
+cylinders of radii R_i = 64 and R_o = 256 about the centre node of a 517 x 517 lattice;
+a gas layer of (R_o - R_i)/4 at the inner cylinder, liquid out to the outer one; an
+angular driving force of magnitude F_o r^2 / R_o^2, F_o = 3e-5, counter-clockwise.  The
+virtual wall density is rho_s = rho_g (the paper names none for this case).
+
+The interfaces are equilibrated without force, the run restarts from that density with
+the Eq. (u.annular) velocity of it and steps to a steady state (tests/table1.py's
+converge()).  Err (Sec. 3.1's norm) compares the tangential velocity with Eq. (u.annular)
+integrated with the converged density, separately along the horizontal ray and the
+45-degree ray from the centre, as Sec. 3.2 does.
+
+Run as `python -m tests.annular [--precision f32|f64]` (one JSON line per scheme).
+"""
+import argparse
+import json
+import math
+import sys
+import time
+
+import numpy as np
+
+from oracle import analytic as A
+from paper_2604_13407_gb300 import inputs as I
+from tests.setups import vdw_case, vdw_params
+from tests.table1 import converge, psi_real_limit
+
+N, R_I, R_O = 517, 64.0, 256.0
+T_R, EPS, TAU = 0.5, 1.895, 0.8
+F_O = 3e-5
+EQUILIBRATION_STEPS = 20000
+C = (N - 1) / 2.0
+
+
+def geometry():
+    solid, wall_u, q = I.annulus(N, N, R_I, R_O)
+    y, x = np.mgrid[0:N, 0:N].astype(np.float64)
+    x -= C
+    y -= C
+    r = np.hypot(x, y)
+    return solid, q, x, y, r
+
+
+def force_field(x, y, r, solid):
+    F = F_O * r * r / R_O**2
+    with np.errstate(invalid="ignore", divide="ignore"):
+        fx = np.where(r > 0, -F * y / r, 0.0)
+        fy = np.where(r > 0, F * x / r, 0.0)
+    fx[solid == 1] = 0.0
+    fy[solid == 1] = 0.0
+    return np.stack([fx, fy])
+
+
+def rays(r):
+    """Node indices and radii of the fluid nodes on the horizontal ray (y = c, x > c) and
+    on the 45-degree ray (x = y > c)."""
+    k = np.arange(1, N // 2 + 1)
+    ci = int(C)
+    h = [(ci, ci + kk) for kk in k if R_I < kk < R_O]
+    d = [(ci + kk, ci + kk) for kk in k if R_I < kk * math.sqrt(2.0) < R_O]
+    return {"horizontal": (np.array(h), np.array([r[a, b] for a, b in h]), (0.0, 1.0)),
+            "diagonal": (np.array(d), np.array([r[a, b] for a, b in d]), (-1.0 / math.sqrt(2.0), 1.0 / math.sqrt(2.0)))}
+
+
+def run(lbm, scheme, precision, tol, max_chunks, log=None):
+    from tests import gpu_cases as GC
+    T, rg, rl = vdw_case(T_R)
+    solid, q, x, y, r = geometry()
+    op = vdw_params(EPS, T_R, nx=N, ny=N, periodic_x=True, periodic_y=True, force_mode=2,
+                    scheme=scheme, tau_l=TAU, tau_g=TAU)
+    nu_fn = lambda rr: A.nu_of_rho(rr, op.tau_l, op.tau_g, op.rho_l, op.rho_g)
+    F_fn = lambda s: F_O * s * s / R_O**2
+
+    def make(field):
+        gp = GC.gpu_params(op, precision)
+        gp.rho_max = psi_real_limit(op, rl)
+        sim = lbm.Simulation(gp)
+        sim.set_geometry(solid, None, q, field)
+        return sim
+
+    r_if = R_I + 0.25 * (R_O - R_I)
+    rho0 = 0.5 * (rl + rg) + 0.5 * (rl - rg) * np.tanh(2.0 * (r - r_if) / 4.0)
+    rho0[solid == 1] = rg
+    sim = make(np.zeros((2, N, N)))
+    sim.init_fields(rho0)
+    sim.step(EQUILIBRATION_STEPS)
+    rho, _, _ = sim.moments()
+    # the theory velocity of the horizontal ray's density, as the initial field
+    R = rays(r)
+    idx, rr, _ = R["horizontal"]
+    u_h = A.annular_theory(rr, rho[idx[:, 0], idx[:, 1]], F_fn, nu_fn, R_I, R_O)
+    ut = np.interp(r, rr, u_h)
+    ut[(r <= R_I) | (r >= R_O)] = 0.0
+    with np.errstate(invalid="ignore", divide="ignore"):
+        ux0 = np.where(r > 0, -ut * y / r, 0.0)
+        uy0 = np.where(r > 0, ut * x / r, 0.0)
+    sim = make(force_field(x, y, r, solid))
+    sim.init_fields(rho, ux0, uy0)
+    nu = (TAU - 0.5) / 3.0
+    change, steps = converge(sim, int(0.25 * (R_O - R_I) ** 2 / nu), tol, max_chunks, log=log)
+    rho, ux, uy = sim.moments()
+    out = {}
+    for name, (idx, rr, (tx, ty)) in R.items():
+        ii, jj = idx[:, 0], idx[:, 1]
+        u_sim = tx * ux[ii, jj] + ty * uy[ii, jj]
+        u_th = A.annular_theory(rr, rho[ii, jj], F_fn, nu_fn, R_I, R_O)
+        band = np.abs(rr - r_if) < 8.0
+        out[name] = {"Err": A.err_norm(u_sim, u_th),
+                     "max_dev_interface_over_U": float(np.abs(u_sim - u_th)[band].max() / np.abs(u_th).max()),
+                     "U": float(np.abs(u_th).max())}
+    return out, change, steps, float(rho[solid == 0].max() / rho[solid == 0].min())
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--precision", choices=("f32", "f64"), default="f32")
+    ap.add_argument("--tol", type=float, default=1e-6)
+    ap.add_argument("--max-chunks", type=int, default=60)
+    ap.add_argument("--scheme", type=int, nargs="*", default=[0, 1])
+    ap.add_argument("--log", action="store_true")
+    args = ap.parse_args()
+    import torch
+    torch.cuda.set_device(0)
+    from paper_2604_13407_gb300 import lbm
+    precision = {"f32": lbm.F32, "f64": lbm.F64}[args.precision]
+    for scheme in args.scheme:
+        t0 = time.time()
+        log = (lambda st, c: print(st, c, file=sys.stderr, flush=True)) if args.log else None
+        out, change, steps, ratio = run(lbm, scheme, precision, args.tol, args.max_chunks, log)
+        print(json.dumps({"case": "annular", "scheme": ["original", "improved"][scheme], "precision": args.precision,
+                          "rays": out, "density_ratio": ratio, "last_chunk_change": change, "steps": steps,
+                          "seconds": round(time.time() - t0, 1)}), flush=True)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -234,7 +234,10 @@ def main():
     ap.add_argument("--scheme", type=int, nargs="*", default=[0, 1])
     ap.add_argument("--eps", type=float, nargs="*", default=[c[0] for c in CASES])
     ap.add_argument("--log", action="store_true", help="per-chunk change on stderr")
+    ap.add_argument("--equilibration", type=int, default=None, help="steps without force")
     args = ap.parse_args()
+    if args.equilibration is not None:
+        globals()["EQUILIBRATION_STEPS"] = args.equilibration
     import torch
     torch.cuda.set_device(0)
     from paper_2604_13407_gb300 import lbm
