@@ -156,7 +156,8 @@ LBM_API lbm_status lbm_create(const lbm_params *p, void *cuda_stream, lbm_ctx **
 LBM_API lbm_status lbm_destroy(lbm_ctx *ctx);
 
 /* Geometry, host arrays (each may be NULL):
- *   solid[ny*nx]          1 = solid node (wall); its psi is psi(rho_s)
+ *   solid[ny*nx]          1 = solid node (wall); its psi is psi(rho_s), or that of its
+ *                         own density when lbm_set_wall_density has set one
  *   wall_u[2*ny*nx]       velocity of each solid node; a link from a fluid node into a
  *                         moving solid gets the term 2 w rho_w (e.u_w)/c_s^2
  *   q[8*ny*nx]            q[(d-1)*ny*nx + node]: wall position on the link from a fluid
@@ -166,6 +167,15 @@ LBM_API lbm_status lbm_destroy(lbm_ctx *ctx);
  * Passing NULL clears the corresponding array.  Call before stepping. */
 LBM_API lbm_status lbm_set_geometry(lbm_ctx *ctx, const uint8_t *solid, const double *wall_u,
                             const double *q, const double *force_field);
+
+/* Virtual density of each solid node, a host array [ny*nx] read at solid nodes only (the
+ * wettability of each wall: Sec. 3 gives every wall psi(rho_s) with one rho_s; this sets
+ * rho_s node by node, e.g. a gas-wetted inner and a liquid-wetted outer cylinder).  Every
+ * entry must be positive with psi(entry) real (LBM_EINVAL otherwise; the previous field
+ * is kept).  Walls beyond a non-periodic edge keep rho_s.  NULL restores rho_s at every
+ * wall.  lbm_get_moments reports the field at solid nodes.  lbm_adjoint_step rejects a
+ * context with a field set (LBM_ENOTSUP).  Call before stepping. */
+LBM_API lbm_status lbm_set_wall_density(lbm_ctx *ctx, const double *wall_rho);
 
 /* Set the populations to the equilibrium f_bar = M^-1 m_eq(rho, u) of each node.
  * rho, ux, uy: [ny*nx] doubles (ux, uy may be NULL for u = 0).  Resets the step count. */

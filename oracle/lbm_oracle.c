@@ -76,6 +76,7 @@ typedef struct {
     double *wall_u;      /* 2n (x plane then y plane), velocity of solid nodes, or NULL */
     double *q;           /* 8n: q[(d-1) n + node] = wall distance fraction on link d, or NULL */
     double *fext;        /* 2n: external force density field (force_mode 2), or NULL */
+    double *wall_rho;    /* n: virtual density of each solid node, or NULL (all walls rho_s) */
     double *fpull;       /* 9n scratch: pulled (pre-collision) populations */
     double *rho, *jx, *jy, *psi;
     double drag[2];
@@ -360,6 +361,7 @@ void or_destroy(or_sim *s)
     free(s->wall_u);
     free(s->q);
     free(s->fext);
+    free(s->wall_rho);
     free(s);
 }
 
@@ -382,6 +384,15 @@ void or_set_geometry(or_sim *s, const uint8_t *solid, const double *wall_u, cons
     s->wall_u = (double *)dup_or_null(wall_u, (size_t)(2 * s->n) * sizeof(double));
     s->q = (double *)dup_or_null(q, (size_t)(8 * s->n) * sizeof(double));
     s->fext = (double *)dup_or_null(fext, (size_t)(2 * s->n) * sizeof(double));
+}
+
+/* Virtual density per solid node (the wettability of each wall, after Benzi et al.'s
+ * virtual-density walls that Sec. 3 uses with one value rho_s); NULL restores rho_s for
+ * every wall.  Walls beyond a non-periodic edge keep rho_s. */
+void or_set_wall_density(or_sim *s, const double *wall_rho)
+{
+    free(s->wall_rho);
+    s->wall_rho = (double *)dup_or_null(wall_rho, (size_t)s->n * sizeof(double));
 }
 
 /* Initial state: f_bar = M^-1 m_eq(rho0, u0) at fluid nodes (the paper does not state
@@ -415,9 +426,10 @@ static void pull_moments_psi(or_sim *s)
         for (int x = 0; x < nx; ++x) {
             int64_t k = node_of(s, x, y);
             if (s->solid && s->solid[k]) {
-                s->rho[k] = s->p.rho_s;
+                const double rs = s->wall_rho ? s->wall_rho[k] : s->p.rho_s;
+                s->rho[k] = rs;
                 s->jx[k] = s->jy[k] = 0.0;
-                s->psi[k] = or_psi(&s->p, s->p.rho_s);
+                s->psi[k] = or_psi(&s->p, rs);
                 continue;
             }
             double rho = 0.0, jx = 0.0, jy = 0.0;
@@ -443,11 +455,11 @@ static void pull_moments_psi(or_sim *s)
     free(row_mom);
 }
 
-/* psi of a neighbour: psi(rho_s) for walls (virtual density, Sec. 3) */
+/* psi of a neighbour: psi(rho_s) beyond a non-periodic edge (virtual density, Sec. 3);
+ * a solid node holds the psi of its own virtual density, set by pull_moments_psi */
 static double psi_at(const or_sim *s, int x, int y)
 {
-    if (is_wall(s, x, y)) return or_psi(&s->p, s->p.rho_s);
-    wrap(s, &x, &y);
+    if (!wrap(s, &x, &y)) return or_psi(&s->p, s->p.rho_s);
     return s->psi[node_of(s, x, y)];
 }
 

@@ -45,6 +45,7 @@ def _load():
         lib.or_create.argtypes = [P(OrParams)]
         lib.or_destroy.argtypes = [ctypes.c_void_p]
         lib.or_set_geometry.argtypes = [ctypes.c_void_p, P(ctypes.c_uint8), dp, dp, dp]
+        lib.or_set_wall_density.argtypes = [ctypes.c_void_p, dp]
         lib.or_init.argtypes = [ctypes.c_void_p, dp, dp, dp]
         lib.or_set_state.argtypes = [ctypes.c_void_p, dp]
         lib.or_get_state.argtypes = [ctypes.c_void_p, dp]
@@ -177,7 +178,7 @@ def collide_node(params: Params, f, psi_x, S, Fext=(0.0, 0.0)):
 class OracleSim:
     """FP64 oracle simulation on the CPU."""
 
-    def __init__(self, params: Params, solid=None, wall_u=None, q=None, fext=None):
+    def __init__(self, params: Params, solid=None, wall_u=None, q=None, fext=None, wall_rho=None):
         self.params = params
         self._c = params.c_struct()
         self.n = params.nx * params.ny
@@ -186,6 +187,7 @@ class OracleSim:
         if not self._h:
             raise MemoryError("oracle allocation failed")
         self.set_geometry(solid, wall_u, q, fext)
+        self.set_wall_density(wall_rho)
 
     def __del__(self):
         h = getattr(self, "_h", None)
@@ -201,6 +203,12 @@ class OracleSim:
         self._fext = _f64(fext, 2 * n)
         sp = None if self._solid is None else self._solid.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8))
         _load().or_set_geometry(self._h, sp, _dp(self._wall_u), _dp(self._q), _dp(self._fext))
+
+    def set_wall_density(self, wall_rho=None):
+        """Virtual density of every solid node ([ny, nx]; read at solid nodes only), or None
+        for rho_s at every wall."""
+        self._wall_rho = _f64(wall_rho, self.n)
+        _load().or_set_wall_density(self._h, _dp(self._wall_rho))
 
     def init(self, rho, ux=None, uy=None):
         n = self.n

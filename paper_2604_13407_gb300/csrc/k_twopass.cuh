@@ -16,7 +16,8 @@ struct GlobalAt {
 };
 
 // psi of the neighbour along e_i of (x, y), read from the psi field written by the psi
-// pass (walls beyond a non-periodic edge: psi(rho_s); solid nodes hold psi(rho_s)).
+// pass (walls beyond a non-periodic edge: psi(rho_s); solid nodes hold the psi of their
+// virtual density, rho_s or the per-node wall density).
 template <class R>
 struct FieldPsi {
     const KParams &kp;
@@ -47,7 +48,7 @@ __global__ void __launch_bounds__(kRowThreads) k_psi(KParams kp)
     const int64_t node = (int64_t)y * kp.nx + x;
     R *psi = static_cast<R *>(kp.psi);
     if (node_is_solid(kp, node)) {
-        psi[node] = cst<R>(kp).psi_s;
+        psi[node] = kp.wall_psi ? R(kp.wall_psi[node]) : cst<R>(kp).psi_s;
         return;
     }
     R f[9];
@@ -99,7 +100,7 @@ __global__ void __launch_bounds__(kRowThreads) k_moments(KParams kp, double *rho
     const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y;
     if (x >= kp.nx) return;
     const int64_t node = (int64_t)y * kp.nx + x;
-    double r = kp.rho_s, u = 0.0, v = 0.0;
+    double r = kp.wall_rho ? kp.wall_rho[node] : kp.rho_s, u = 0.0, v = 0.0;
     if (!node_is_solid(kp, node)) {
         const R *psi = static_cast<const R *>(kp.psi);
         R f[9], fb[9], Sx, Sy, Fex, Fey, ux, uy;

@@ -110,8 +110,8 @@ lbm_status adjoint_run(lbm_ctx *ctx, int64_t nsteps, int32_t K, int32_t objectiv
         msg = "the adjoint supports FP64 and FP32 storage only";
         return LBM_ENOTSUP;
     }
-    if (v.kp->wall_u || v.kp->q) {
-        msg = "the adjoint supports resting half-way walls only (no wall velocity, no link fractions)";
+    if (v.kp->wall_u || v.kp->q || v.kp->wall_rho) {
+        msg = "the adjoint supports resting half-way walls with one virtual density only";
         return LBM_ENOTSUP;
     }
     if (p.force_mode == LBM_FORCE_FIELD) {

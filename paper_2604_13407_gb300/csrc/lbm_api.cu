@@ -30,6 +30,7 @@ struct lbm_ctx {
     void *psi = nullptr;
     uint8_t *solid = nullptr;
     double *wall_u = nullptr, *q = nullptr, *fext = nullptr;
+    double *wall_rho = nullptr, *wall_psi = nullptr;  // per solid node virtual density, its psi
     double *dacc = nullptr;             // diagnostics accumulators (9 doubles, 1 u64, 1 int)
     double *scratch = nullptr;          // host<->device staging for FP64 field copies
     size_t scratch_bytes = 0;
@@ -233,6 +234,8 @@ static void fill_constants(lbm_ctx *c)
     k.wall_u = c->wall_u;
     k.q = c->q;
     k.fext = c->fext;
+    k.wall_rho = c->wall_rho;
+    k.wall_psi = c->wall_psi;
     k.err = c->derr;
 }
 
@@ -268,7 +271,7 @@ static void free_all(lbm_ctx *c)
     if (!c) return;
     if (c->stream) cudaStreamSynchronize(c->stream);
     void *bufs[] = {c->pops[0], c->pops[1], c->refp[0], c->refp[1], c->psi, c->solid,
-                    c->wall_u, c->q, c->fext, c->dacc, c->scratch, c->derr};
+                    c->wall_u, c->q, c->fext, c->wall_rho, c->wall_psi, c->dacc, c->scratch, c->derr};
     for (void *b : bufs)
         if (b) cudaFree(b);
     adjoint_free(c->adj);
@@ -400,6 +403,30 @@ extern "C" lbm_status lbm_set_geometry(lbm_ctx *c, const uint8_t *solid, const d
     if ((s = upload(c, &c->q, q, 8 * n, "q")) != LBM_OK) return s;
     if ((s = upload(c, &c->fext, force_field, 2 * n, "force_field")) != LBM_OK) return s;
     CK(cudaStreamSynchronize(c->stream), "set_geometry");
+    fill_constants(c);
+    choose_kernel(c);
+    return LBM_OK;
+}
+
+extern "C" lbm_status lbm_set_wall_density(lbm_ctx *c, const double *wall_rho)
+{
+    if (!c) return LBM_EINVAL;
+    const size_t n = (size_t)c->p.nx * c->p.ny;
+    std::vector<double> psi;
+    if (wall_rho) {
+        psi.resize(n);
+        for (size_t k = 0; k < n; ++k) {
+            // the same host evaluation as psi(rho_s), so a uniform field equals the scalar
+            psi[k] = host_psi(c->p, wall_rho[k]);
+            if (!(wall_rho[k] > 0.0) || !(psi[k] > 0.0) || !std::isfinite(psi[k]))
+                return fail(c, LBM_EINVAL, "psi of a wall density is not real and positive");
+        }
+    }
+    lbm_status s;
+    if ((s = upload(c, &c->wall_rho, wall_rho, n, "wall_rho")) != LBM_OK) return s;
+    if ((s = upload(c, &c->wall_psi, wall_rho ? psi.data() : (const double *)nullptr, n, "wall_psi")) != LBM_OK)
+        return s;
+    CK(cudaStreamSynchronize(c->stream), "set_wall_density");
     fill_constants(c);
     choose_kernel(c);
     return LBM_OK;

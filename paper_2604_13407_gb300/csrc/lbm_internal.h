@@ -67,6 +67,8 @@ struct KParams {
     const double *wall_u;  // [2][ny*nx] or null
     const double *q;       // [8][ny*nx] or null
     const double *fext;    // [2][ny*nx] or null
+    const double *wall_rho;  // [ny*nx] virtual density of each solid node, or null (rho_s)
+    const double *wall_psi;  // [ny*nx] psi of wall_rho, or null (psi_s)
     int *err;              // device error word (0 = fine)
     Consts<double> cd;     // constants for FP64 arithmetic
     Consts<float> cf;      // constants for FP32 arithmetic

@@ -68,6 +68,7 @@ def load_library(path=None):
         "lbm_create": (st, [_P(LbmParams), _vp, _P(_vp)]),
         "lbm_destroy": (st, [_vp]),
         "lbm_set_geometry": (st, [_vp, _vp, _vp, _vp, _vp]),
+        "lbm_set_wall_density": (st, [_vp, _vp]),
         "lbm_init_fields": (st, [_vp, _vp, _vp, _vp, ctypes.c_int]),
         "lbm_step": (st, [_vp, ctypes.c_int64]),
         "lbm_get_moments": (st, [_vp, _vp, _vp, _vp, ctypes.c_int]),
@@ -177,6 +178,15 @@ class Simulation:
         pq, _ = _ptr(q, 8 * self.n, np.float64, keep)
         pf, _ = _ptr(force_field, 2 * self.n, np.float64, keep)
         self._check(self.lib.lbm_set_geometry(self._h, ps, pw, pq, pf))
+
+    def set_wall_density(self, wall_rho=None):
+        """Virtual density of each solid node ([ny, nx], read at solid nodes), or None for
+        rho_s at every wall.  A host array: CUDA tensors are copied to the host first."""
+        if wall_rho is not None and hasattr(wall_rho, "cpu"):
+            wall_rho = wall_rho.detach().cpu().numpy()
+        keep = []
+        pr, _ = _ptr(wall_rho, self.n, np.float64, keep)
+        self._check(self.lib.lbm_set_wall_density(self._h, pr))
 
     def init_fields(self, rho, ux=None, uy=None):
         keep = []

@@ -6,7 +6,10 @@ T_r = 0.5 (liquid-to-gas ratio about 113), epsilon = 1.895, tau = 0.8, Lambda = 
 cylinders of radii R_i = 64 and R_o = 256 about the centre node of a 517 x 517 lattice;
 a gas layer of (R_o - R_i)/4 at the inner cylinder, liquid out to the outer one; an
 angular driving force of magnitude F_o r^2 / R_o^2, F_o = 3e-5, counter-clockwise.  The
-virtual wall density is rho_s = rho_g (the paper names none for this case).
+paper names no virtual wall density for this case; the inner cylinder gets rho_g and the
+outer one rho_l (lbm_set_wall_density), each wetted by the phase against it.  One rho_s for
+both fails: the phase against the unlike wall is pulled off it so hard that its density
+leaves the range where the van der Waals psi is real.
 
 The interfaces are equilibrated without force, the run restarts from that density with
 the Eq. (u.annular) velocity of it and steps to a steady state (tests/table1.py's
@@ -80,11 +83,13 @@ def run(lbm, scheme, precision, tol, max_chunks, log=None):
         gp.rho_max = psi_real_limit(op, rl)
         sim = lbm.Simulation(gp)
         sim.set_geometry(solid, None, q, field)
+        sim.set_wall_density(wall_rho)
         return sim
 
+    wall_rho = np.where(r <= R_I, rg, rl)
     r_if = R_I + 0.25 * (R_O - R_I)
     rho0 = 0.5 * (rl + rg) + 0.5 * (rl - rg) * np.tanh(2.0 * (r - r_if) / 4.0)
-    rho0[solid == 1] = rg
+    rho0[solid == 1] = wall_rho[solid == 1]
     sim = make(np.zeros((2, N, N)))
     sim.init_fields(rho0)
     sim.step(EQUILIBRATION_STEPS)

@@ -27,6 +27,7 @@ import numpy as np
 
 from paper_2604_13407_gb300 import inputs as I
 from tests.setups import vdw_case, vdw_params
+from tests.table1 import psi_real_limit
 
 W, H, D = 256, 2048, 128.0
 T_R, EPS, TAU = 0.5, 1.895, 0.8
@@ -36,15 +37,6 @@ RELAX_STEPS = 60000
 # Sec. 3.3: terminal |U_c*| (original, improved) per |g|, and the migration onset
 PAPER_TERMINAL = {0.5e-7: (0.9144, 1.0104), 1.0e-7: (1.2535, 0.9015), 2.0e-7: (1.1116, 1.0928)}
 PAPER_ONSET_2E7 = {"t_star": (107.6, 53.8), "U_c_star": 1.92}
-
-
-def psi_real_limit(op, rho_from):
-    """Largest density above rho_from at which psi = sqrt(2 (p - rho/3)/G) is still real
-    for the van der Waals EOS, less 1 %."""
-    xs = np.linspace(rho_from, (1.0 - 1e-9) / op.b, 200001)
-    p = xs * op.R * op.T / (1.0 - op.b * xs) - op.a * xs * xs
-    bad = np.nonzero(p - xs / 3.0 >= 0.0)[0]
-    return 0.99 * (xs[bad[0]] if len(bad) else xs[-1])
 
 
 def make_sim(lbm, scheme, precision, g, kernel=0):

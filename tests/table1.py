@@ -103,7 +103,7 @@ def psi_real_limit(op, rho_from):
     """Largest density above rho_from up to which psi = sqrt(2 (p - rho/3) / G) stays real
     (G < 0: p_EOS < rho/3) for the van der Waals EOS, less 1 %; p diverges at 1/b."""
     xs = np.linspace(rho_from, (1.0 - 1e-9) / op.b, 200001)
-    p = xs * op.R * op.T / (1.0 - op.b * xs) - op.a * xs * xs
+    p = op.K_eos * (xs * op.R * op.T / (1.0 - op.b * xs) - op.a * xs * xs)
     bad = np.nonzero(p - xs / 3.0 >= 0.0)[0]
     return 0.99 * (xs[bad[0]] if len(bad) else xs[-1])
 
