@@ -47,8 +47,8 @@ def geometry():
     return solid, q, x, y, r
 
 
-def force_field(x, y, r, solid):
-    F = F_O * r * r / R_O**2
+def force_field(x, y, r, solid, F_o=F_O):
+    F = F_o * r * r / R_O**2
     with np.errstate(invalid="ignore", divide="ignore"):
         fx = np.where(r > 0, -F * y / r, 0.0)
         fy = np.where(r > 0, F * x / r, 0.0)
@@ -68,14 +68,14 @@ def rays(r):
             "diagonal": (np.array(d), np.array([r[a, b] for a, b in d]), (-1.0 / math.sqrt(2.0), 1.0 / math.sqrt(2.0)))}
 
 
-def run(lbm, scheme, precision, tol, max_chunks, log=None):
+def run(lbm, scheme, precision, tol, max_chunks, log=None, F_o=F_O):
     from tests import gpu_cases as GC
     T, rg, rl = vdw_case(T_R)
     solid, q, x, y, r = geometry()
     op = vdw_params(EPS, T_R, nx=N, ny=N, periodic_x=True, periodic_y=True, force_mode=2,
                     scheme=scheme, tau_l=TAU, tau_g=TAU)
     nu_fn = lambda rr: A.nu_of_rho(rr, op.tau_l, op.tau_g, op.rho_l, op.rho_g)
-    F_fn = lambda s: F_O * s * s / R_O**2
+    F_fn = lambda s: F_o * s * s / R_O**2
 
     def make(field):
         gp = GC.gpu_params(op, precision)
@@ -96,7 +96,7 @@ def run(lbm, scheme, precision, tol, max_chunks, log=None):
     R = rays(r)
     # the forced run starts from rest: starting at the theory velocity (up to ~0.15 in the
     # gas layer) launches pressure waves that empty the gas layer
-    sim = make(force_field(x, y, r, solid))
+    sim = make(force_field(x, y, r, solid, F_o))
     sim.init_fields(rho)
     nu = (TAU - 0.5) / 3.0
     change, steps = converge(sim, int(0.25 * (R_O - R_I) ** 2 / nu), tol, max_chunks, log=log)
@@ -120,6 +120,7 @@ def main():
     ap.add_argument("--max-chunks", type=int, default=60)
     ap.add_argument("--scheme", type=int, nargs="*", default=[0, 1])
     ap.add_argument("--log", action="store_true")
+    ap.add_argument("--f-o", type=float, default=F_O, help="driving force density at R_o")
     args = ap.parse_args()
     import torch
     torch.cuda.set_device(0)
@@ -128,8 +129,9 @@ def main():
     for scheme in args.scheme:
         t0 = time.time()
         log = (lambda st, c: print(st, c, file=sys.stderr, flush=True)) if args.log else None
-        out, change, steps, ratio = run(lbm, scheme, precision, args.tol, args.max_chunks, log)
+        out, change, steps, ratio = run(lbm, scheme, precision, args.tol, args.max_chunks, log, args.f_o)
         print(json.dumps({"case": "annular", "scheme": ["original", "improved"][scheme], "precision": args.precision,
+                          "F_o": args.f_o,
                           "rays": out, "density_ratio": ratio, "last_chunk_change": change, "steps": steps,
                           "seconds": round(time.time() - t0, 1)}), flush=True)
 
