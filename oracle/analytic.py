@@ -210,6 +210,44 @@ def fde_aligned_residual(rho, Fn, u, Q, F_dri, nu):
     return lhs + F_dri / nu
 
 
+def lb_ana_aligned(rho, Fn, X, kq, F_dri, nu, u_ends=None):
+    """"LB-ana" of Sec. 3.1: the velocity profile that solves Eq. (fde.ali) for a given
+    steady density profile, with Q_m,6 = kq X u (Eq. (qm6.ali): kq = 3 epsilon / 8 for the
+    improved scheme; the original scheme has Q_m,6 = 0, kq = 0).  Fn is the pairwise
+    force along the profile, X = dt^2 F_hat^2 / psi_hat^2 = Fn^2 / (-G psi^2).  Row i reads
+      (rho + 3/2 Fn + kq X)^{i-1} u^{i-1} + (rho - 3/2 Fn + kq X)^{i+1} u^{i+1}
+        - 2 (rho + kq X)^i u^i = -F_dri / nu.
+    The walls are not part of the equation: with u_ends = None each end row sees a mirror
+    ghost node (u = -u of the end node, its coefficients those of the end node with Fn
+    reversed), a half-way no-slip wall; with u_ends = (u_0, u_{N-1}) the end values are
+    given and the interior rows are solved."""
+    rho, Fn, X = (np.asarray(v, dtype=np.float64) for v in (rho, Fn, X))
+    N = len(rho)
+    lo = rho + 1.5 * Fn + kq * X
+    hi = rho - 1.5 * Fn + kq * X
+    M = np.zeros((N, N))
+    b = np.full(N, -F_dri / nu)
+    for i in range(N):
+        M[i, i] = -2.0 * (rho[i] + kq * X[i])
+        if i > 0:
+            M[i, i - 1] = lo[i - 1]
+        else:
+            M[i, i] -= rho[0] - 1.5 * Fn[0] + kq * X[0]
+        if i < N - 1:
+            M[i, i + 1] = hi[i + 1]
+        else:
+            M[i, i] -= rho[-1] + 1.5 * Fn[-1] + kq * X[-1]
+    if u_ends is not None:
+        u0, u1 = u_ends
+        inner = slice(1, N - 1)
+        bi = b[inner] - M[inner, 0] * u0 - M[inner, N - 1] * u1
+        u = np.empty(N)
+        u[0], u[-1] = u0, u1
+        u[inner] = np.linalg.solve(M[inner, inner], bi)
+        return u
+    return np.linalg.solve(M, b)
+
+
 def fde_oblique_residual(rho, Fx, u_beta, Q46, F_dri, nu):
     """Eq. (fde.obl) at interior indices 1..N-2, with i the index along alpha
     (node spacing dx/sqrt 2), Fx the x component of the pairwise force, u_beta the
