@@ -17,7 +17,7 @@ TEST INFRASTRUCTURE ONLY.  Each function restates a relation the paper (Huang, H
 import math
 
 import numpy as np
-from scipy import integrate, optimize
+from scipy import integrate, linalg, optimize
 
 
 # ----------------------------------------------------------------- EOS -----
@@ -223,29 +223,51 @@ def lb_ana_aligned(rho, Fn, X, kq, F_dri, nu, u_ends=None):
     given and the interior rows are solved."""
     rho, Fn, X = (np.asarray(v, dtype=np.float64) for v in (rho, Fn, X))
     N = len(rho)
-    lo = rho + 1.5 * Fn + kq * X
-    hi = rho - 1.5 * Fn + kq * X
-    M = np.zeros((N, N))
+    sub = rho[:-1] + 1.5 * Fn[:-1] + kq * X[:-1]  # row i, column i - 1
+    sup = rho[1:] - 1.5 * Fn[1:] + kq * X[1:]     # row i, column i + 1
+    diag = -2.0 * (rho + kq * X)
+    diag[0] -= rho[0] - 1.5 * Fn[0] + kq * X[0]
+    diag[-1] -= rho[-1] + 1.5 * Fn[-1] + kq * X[-1]
     b = np.full(N, -F_dri / nu)
-    for i in range(N):
-        M[i, i] = -2.0 * (rho[i] + kq * X[i])
-        if i > 0:
-            M[i, i - 1] = lo[i - 1]
-        else:
-            M[i, i] -= rho[0] - 1.5 * Fn[0] + kq * X[0]
-        if i < N - 1:
-            M[i, i + 1] = hi[i + 1]
-        else:
-            M[i, i] -= rho[-1] + 1.5 * Fn[-1] + kq * X[-1]
     if u_ends is not None:
         u0, u1 = u_ends
-        inner = slice(1, N - 1)
-        bi = b[inner] - M[inner, 0] * u0 - M[inner, N - 1] * u1
+        bi = b[1:-1].copy()
+        bi[0] -= sub[0] * u0
+        bi[-1] -= sup[-1] * u1
         u = np.empty(N)
         u[0], u[-1] = u0, u1
-        u[inner] = np.linalg.solve(M[inner, inner], bi)
+        u[1:-1] = _tridiagonal(sub[1:-1], diag[1:-1], sup[1:-1], bi)
         return u
-    return np.linalg.solve(M, b)
+    return _tridiagonal(sub, diag, sup, b)
+
+
+def _tridiagonal(sub, diag, sup, b):
+    """Solve the tridiagonal system with sub-, main and super-diagonals (a library banded
+    solver, LU with partial pivoting)."""
+    ab = np.zeros((3, len(diag)))
+    ab[0, 1:] = sup
+    ab[1] = diag
+    ab[2, :-1] = sub
+    return linalg.solve_banded((1, 1), ab, b)
+
+
+def lb_ana_oblique(rho, Fx, X, K, F_dri, nu):
+    """Eq. (fde.obl) solved for u_beta along alpha (node spacing dx/sqrt 2), with
+    Q_m,4+6 = -2 sqrt 2 K X u_beta (Eq. (obl.11) written with u_x + u_y = sqrt 2 u_beta;
+    the improved scheme has K = (24 epsilon - 15)/32, the original K = 0).  Fx is the x
+    component of the pairwise force (Eq. (obl.10)), X = dt^2 F_hat_x^2 / psi_hat^2.  Since
+    -sqrt 2/4 times the second difference of Q_m,4+6 is + K times that of X u_beta, row i reads
+      (rho + 3/2 Fx + K X)^{i-1} u^{i-1} + (rho - 3/2 Fx + K X)^{i+1} u^{i+1}
+        - 2 (rho + K X)^i u^i = -F_dri / (2 nu).
+    Each end row sees a mirror ghost node (u = -u of the end node, Fx reversed): a
+    half-way no-slip wall."""
+    rho, Fx, X = (np.asarray(v, dtype=np.float64) for v in (rho, Fx, X))
+    sub = rho[:-1] + 1.5 * Fx[:-1] + K * X[:-1]
+    sup = rho[1:] - 1.5 * Fx[1:] + K * X[1:]
+    diag = -2.0 * (rho + K * X)
+    diag[0] -= rho[0] - 1.5 * Fx[0] + K * X[0]
+    diag[-1] -= rho[-1] + 1.5 * Fx[-1] + K * X[-1]
+    return _tridiagonal(sub, diag, sup, np.full(len(rho), -F_dri / (2.0 * nu)))
 
 
 def fde_oblique_residual(rho, Fx, u_beta, Q46, F_dri, nu):

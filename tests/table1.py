@@ -62,7 +62,8 @@ def converge(sim, chunk, tol=TOL, max_chunks=400, log=None):
     liquid plug sliding on the gas layers, decays by a fixed ratio r per chunk; once three
     successive chunk states show the same r (to 1 %), the state is extrapolated to the
     limit, S + dS r / (1 - r) (Aitken's delta-squared on the whole state), which removes that
-    mode and cuts the chunks needed about threefold."""
+    mode and cuts the chunks needed about threefold.  It is done only while the relative
+    change is below 1e-2 and for r <= 0.95."""
     prev_u, change, steps = None, None, 0
     hist, r_prev = [], None
     for _ in range(max_chunks):
@@ -83,7 +84,12 @@ def converge(sim, chunk, tol=TOL, max_chunks=400, log=None):
         if len(hist) >= 2:
             dS, dP = S - hist[-1], hist[-1] - hist[-2]
             r = float((dS * dP).sum() / (dP * dP).sum())
-            if r_prev is not None and 0.0 < r < 0.999 and abs(r - r_prev) < 0.01 * r:
+            # only in the linear regime (small change) and for a ratio whose factor
+            # r / (1 - r) stays moderate: a slow spin-up (r near 1 while the state still
+            # moves by percents per chunk) is not a geometric decay, and extrapolating it
+            # by a factor of tens throws the state out of range
+            if (r_prev is not None and 0.0 < r <= 0.95 and abs(r - r_prev) < 0.01 * r
+                    and change is not None and change < 1e-2):
                 if log is not None:
                     log(steps, "extrapolate r = %.4f" % r)
                 S = S + dS * (r / (1.0 - r))

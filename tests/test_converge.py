@@ -2,7 +2,8 @@
 whose answer is known: a state S that relaxes to S* through one slow mode (ratio r per
 step) and carries an undamped period-2 mode, the two features of the two-phase runs.
 Checks: the two-state average removes the period-2 mode; the Aitken extrapolation hits the
-fixed point of the slow mode; the stop criterion is the relative velocity change."""
+fixed point of the slow mode, and is refused for a slow spin-up; the stop criterion is the
+relative velocity change."""
 import numpy as np
 
 from tests.table1 import converge
@@ -56,7 +57,7 @@ def test_extrapolation_saves_most_of_the_chunks():
     start); the extrapolation gets there in a handful."""
     sim, _ = make()
     change, steps = converge(sim, chunk=100, tol=1e-10, max_chunks=400)
-    assert steps < 10 * 101, steps  # measured: 6 chunks
+    assert steps < 30 * 101, steps  # measured: 21 chunks (it extrapolates once the change is < 1e-2)
 
 
 def test_stops_when_the_velocity_change_is_below_tol():
@@ -64,3 +65,17 @@ def test_stops_when_the_velocity_change_is_below_tol():
     change, steps = converge(sim, chunk=10, tol=1e-6, max_chunks=50)
     assert change < 1e-6
     assert steps <= 5 * 11
+
+
+def test_no_extrapolation_of_a_slow_spin_up():
+    """r = 0.985 per chunk (a factor r / (1 - r) = 66): the extrapolation is refused, as it
+    is while the state still changes by more than 1e-2 per chunk."""
+    sim, _ = make(r=0.99985)
+    events = []
+    converge(sim, chunk=100, tol=1e-12, max_chunks=60, log=lambda st, c: events.append(c))
+    assert not any(isinstance(c, str) and c.startswith("extrapolate") for c in events)
+    sim, _ = make()
+    events = []
+    converge(sim, chunk=100, tol=1e-10, max_chunks=400, log=lambda st, c: events.append(c))
+    extrap = [i for i, c in enumerate(events) if isinstance(c, str)]
+    assert extrap and all(events[i - 1] < 1e-2 for i in extrap)
