@@ -1,7 +1,8 @@
 """Writes table1_aligned_oracle.json: Err of the grid-aligned two-phase Poiseuille flow of
 Sec. 3.1 (Table 1) from the FP64 CPU oracle, all twelve aligned cases (epsilon 0, 1, 2;
 tau 0.8, 1.5; original and improved Q_m), each run to a relative velocity change below
-1e-7 per quarter viscous time by tests/table1.py's converge().  Only oracle/ computes.
+1e-7 per quarter viscous time by tests/table1.py's converge(), and, for tau = 1.5, the
+converged rho and u across the channel.  Only oracle/ computes.
 
 Run from the repository root: `python -m tests.golden.make_table1_oracle` (about ten
 minutes on eight cores; one process per case, single-threaded each)."""
@@ -17,7 +18,12 @@ def one(args):
     os.environ["OMP_NUM_THREADS"] = "1"
     from tests import table1 as T
     eps, t_r, tau, scheme = args
-    return T.record(T.OracleBackend(), "aligned", eps, t_r, tau, scheme)
+    row = T.record(T.OracleBackend(), "aligned", eps, t_r, tau, scheme)
+    if tau == 1.5:  # the converged profiles, for the LB-ana check of Eq. (fde.ali)
+        prof = {}
+        T.run_aligned(T.OracleBackend(), eps, t_r, tau, scheme, profiles=prof)
+        row["profiles"] = prof
+    return row
 
 
 def main():

@@ -163,10 +163,12 @@ class OracleBackend:
         return _OracleRun(O.OracleSim(op, solid=solid))
 
 
-def run_aligned(backend, eps, t_r, tau, scheme, width=WIDTH_ALIGNED, tol=TOL, max_chunks=400, log=None):
+def run_aligned(backend, eps, t_r, tau, scheme, width=WIDTH_ALIGNED, tol=TOL, max_chunks=400, log=None,
+                profiles=None):
     """Grid-aligned channel: equilibrate the interfaces without force, restart from the
     equilibrated density with the Eq. (u.plane) velocity of that density, converge.
-    Returns Err, the last relative change, the steps and the liquid-to-gas ratio."""
+    Returns Err, the last relative change, the steps and the liquid-to-gas ratio; the
+    converged rho and u across the channel go into the dict `profiles` when one is given."""
     T, rg, rl = vdw_case(t_r)
     nx = backend.aligned_nx
     mk = lambda F: vdw_params(eps, t_r, nx=nx, ny=width, periodic_x=True, periodic_y=False, Fx=F,
@@ -182,6 +184,9 @@ def run_aligned(backend, eps, t_r, tau, scheme, width=WIDTH_ALIGNED, tol=TOL, ma
     nu = (tau - 0.5) / 3.0
     change, steps = converge(sim, int(0.25 * width * width / nu), tol, max_chunks, log=log)
     rho, ux, _ = sim.moments()
+    if profiles is not None:
+        profiles["rho"] = [float(v) for v in rho[:, 0]]
+        profiles["u"] = [float(v) for v in ux[:, 0]]
     th = A.poiseuille_theory(rho[:, 0], F_DRIVE, nu_fn(op))
     return A.err_norm(ux[:, 0], th), change, steps, float(rho[:, 0].max() / rho[:, 0].min())
 
