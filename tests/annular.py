@@ -1,5 +1,9 @@
-"""Two-phase annular shear flow of Sec. 3.2 on the GPU library, with interpolated
-(Bouzidi) bounce-back on the two cylinders in place of the paper's wall scheme.
+"""Two-phase annular shear flow of Sec. 3.2 on the GPU library, with half-way bounce-back
+on the staircase cylinders in place of the paper's wall scheme.  Interpolated (Bouzidi)
+bounce-back (--interpolated) does not conserve mass: on this annulus, with liquid of
+density 8.6 against the outer cylinder, it loses 4.5 % of the fluid mass in 3e5 steps at
+quarter scale, the interface drifts and the flow never settles; half-way links conserve it
+exactly.
 
 Set-up (Sec. 3.2): van der Waals EOS (a = 9/49, b = 2/21, R = 1, K_EOS = 1/16) at
 T_r = 0.5 (liquid-to-gas ratio about 113), epsilon = 1.895, tau = 0.8, Lambda = 1/12;
@@ -18,8 +22,7 @@ density, separately along the horizontal ray and the 45-degree ray from the cent
 Sec. 3.2 does.
 
 At the printed F_o the theory puts the gas layer near 0.13, about the isothermal sound
-speed of this van der Waals gas, and the runs have not reached a steady state (they end in
-NaN); --f-o sets a smaller driving force.
+speed of this van der Waals gas; --f-o sets a smaller driving force.
 
 Run as `python -m tests.annular [--precision f32|f64] [--f-o F]` (one JSON line per scheme).
 """
@@ -73,7 +76,7 @@ def rays(r):
             "diagonal": (np.array(d), np.array([r[a, b] for a, b in d]), (-1.0 / math.sqrt(2.0), 1.0 / math.sqrt(2.0)))}
 
 
-def run(lbm, scheme, precision, tol, max_chunks, log=None, F_o=F_O):
+def run(lbm, scheme, precision, tol, max_chunks, log=None, F_o=F_O, interpolated=False):
     """One scheme: equilibrate, force from rest, converge; Err and the largest deviation
     from the theory within 8 nodes of the interface, per ray."""
     from tests import gpu_cases as GC
@@ -88,7 +91,7 @@ def run(lbm, scheme, precision, tol, max_chunks, log=None, F_o=F_O):
         gp = GC.gpu_params(op, precision)
         gp.rho_max = psi_real_limit(op, rl)
         sim = lbm.Simulation(gp)
-        sim.set_geometry(solid, None, q, field)
+        sim.set_geometry(solid, None, q if interpolated else None, field)
         sim.set_wall_density(wall_rho)
         return sim
 
@@ -128,6 +131,7 @@ def main():
     ap.add_argument("--scheme", type=int, nargs="*", default=[0, 1])
     ap.add_argument("--log", action="store_true")
     ap.add_argument("--f-o", type=float, default=F_O, help="driving force density at R_o")
+    ap.add_argument("--interpolated", action="store_true", help="Bouzidi links on the circles")
     args = ap.parse_args()
     import torch
     torch.cuda.set_device(0)
@@ -136,9 +140,10 @@ def main():
     for scheme in args.scheme:
         t0 = time.time()
         log = (lambda st, c: print(st, c, file=sys.stderr, flush=True)) if args.log else None
-        out, change, steps, ratio = run(lbm, scheme, precision, args.tol, args.max_chunks, log, args.f_o)
+        out, change, steps, ratio = run(lbm, scheme, precision, args.tol, args.max_chunks, log, args.f_o,
+                                        args.interpolated)
         print(json.dumps({"case": "annular", "scheme": ["original", "improved"][scheme], "precision": args.precision,
-                          "F_o": args.f_o,
+                          "F_o": args.f_o, "walls": "interpolated" if args.interpolated else "half-way",
                           "rays": out, "density_ratio": ratio, "last_chunk_change": change, "steps": steps,
                           "seconds": round(time.time() - t0, 1)}), flush=True)
 
