@@ -163,6 +163,9 @@ LBM_API lbm_status lbm_destroy(lbm_ctx *ctx);
  *   q[8*ny*nx]            q[(d-1)*ny*nx + node]: wall position on the link from a fluid
  *                         node along e_d, as a fraction of the link (0, 1]; 1/2 is
  *                         half-way bounce-back, other values interpolated bounce-back
+ *                         (linear, Bouzidi: second order for the velocity but not mass
+ *                         conserving; against a dense liquid the fluid mass drifts, while
+ *                         half-way links conserve it to round-off)
  *   force_field[2*ny*nx]  force density of LBM_FORCE_FIELD
  * Passing NULL clears the corresponding array.  Call before stepping. */
 LBM_API lbm_status lbm_set_geometry(lbm_ctx *ctx, const uint8_t *solid, const double *wall_u,
