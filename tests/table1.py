@@ -17,7 +17,7 @@ almost as a plug held back by the thin gas layers, so the flow relaxes over many
 times W^2 / nu.  The interfaces are first equilibrated without force; the run then restarts
 from that density with the Eq. (u.plane) velocity of it and steps until the velocity changes
 by less than 1e-7 (relative) over a quarter viscous time (converge() below).  The runs are
-FP64 (in FP32 the oblique flow never settles: the change stalls at 1e-4 per chunk).  Err is
+FP64 (FP32 oblique runs have not settled within 60 chunks: the change stalled at 1e-4).  Err is
 Sec. 3.1's relative error of the velocity along the walls against Eq. (u.plane) integrated
 with the converged density profile.  The 45-degree interfaces need a far longer force-free
 equilibration than the aligned ones (--equilibration 200000 at 256^2).
