@@ -54,7 +54,8 @@ def build(force: bool = False, verbose: bool = False) -> str:
     def compile_one(item):
         name, extra = item
         obj = os.path.join(OUT, name.replace(".cu", ".o"))
-        cmd = [nvcc] + ARCH + COMMON + extra + ["-c", os.path.join(CSRC, name), "-o", obj]
+        defs = os.environ.get("LBM_NVCC_DEFS", "").split()  # e.g. "-DLBM_F32_IEEE=1"
+        cmd = [nvcc] + ARCH + COMMON + extra + defs + ["-c", os.path.join(CSRC, name), "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError("nvcc failed for %s:\n%s\n%s" % (name, " ".join(cmd), r.stderr))

@@ -14,34 +14,18 @@
 // nodes.  Reciprocal and square root stay per node.  A warp covers 64 columns: lanes
 // 1..30 update 60 columns, lanes 0 and 31 carry the halo columns.
 //
-// The collision evaluates the same formulas as `collide` (lbm_device.cuh), in packed form
-// and with shared subexpressions, so results agree with the two-pass step to FP32
-// rounding (not bit for bit).  The storage codec rounds exactly as `Codec<>`: the
-// deviation (f - w_i rho_ref) 2^k is formed as one fused multiply-add of f 2^k and
-// -(w_i rho_ref) 2^k, which equals the rounded difference times the power of two.
+// Density, psi, stencil and collision are the FP32 formulation of lbm_f32.cuh evaluated on
+// packed pairs; the two-pass step evaluates the same expressions on single nodes, and the
+// two agree to FP32 rounding (the compiler fuses some packed multiply-add chains).  The
+// storage codec rounds exactly as
+// `Codec<>`: the deviation (f - w_i rho_ref) 2^k is formed as one fused multiply-add of
+// f 2^k and -(w_i rho_ref) 2^k, which equals the rounded difference times the power of
+// two.
 #pragma once
 
 #include "k_fused.cuh"
 
 namespace lbm {
-
-// ------------------------------------------------------- packed FP32 pairs --
-struct v2 {
-    float2 v;
-};
-__device__ __forceinline__ v2 V(float a, float b) { return v2{make_float2(a, b)}; }
-__device__ __forceinline__ v2 S2(float a) { return v2{make_float2(a, a)}; }
-__device__ __forceinline__ v2 operator+(v2 a, v2 b) { return v2{__fadd2_rn(a.v, b.v)}; }
-__device__ __forceinline__ v2 operator*(v2 a, v2 b) { return v2{__fmul2_rn(a.v, b.v)}; }
-__device__ __forceinline__ v2 operator-(v2 a, v2 b)
-{
-    unsigned long long ra = *reinterpret_cast<unsigned long long *>(&a.v), rb = *reinterpret_cast<unsigned long long *>(&b.v), rd;
-    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(rd) : "l"(ra), "l"(rb));
-    return v2{*reinterpret_cast<float2 *>(&rd)};
-}
-__device__ __forceinline__ v2 fma2(v2 a, v2 b, v2 c) { return v2{__ffma2_rn(a.v, b.v, c.v)}; }
-__device__ __forceinline__ v2 rcp2(v2 a) { return V(1.0f / a.v.x, 1.0f / a.v.y); }
-__device__ __forceinline__ v2 sqrt2(v2 a) { return V(sqrtf(a.v.x), sqrtf(a.v.y)); }
 
 // ------------------------------------------------------------ staging --------
 template <class S, int NW, int RING>
@@ -114,133 +98,6 @@ __device__ __forceinline__ v2 load_ref_pair(const float *p, int off)
 
 // ------------------------------------------------------------ physics --------
 #define LBM_C2(name) v2{q.name}
-// Literal constants: immediates (LBM_PAIR_IMM = 1) or pairs from the kernel parameters.
-#ifndef LBM_PAIR_IMM
-#define LBM_PAIR_IMM 1
-#endif
-#if LBM_PAIR_IMM
-#define LBM_K(name, val) S2(val)
-#define LBM_KP(name, val) S2(val)
-#else
-#define LBM_K(name, val) v2{q.name}
-#define LBM_KP(name, val) v2{kp.c2.name}
-#endif
-
-// psi = sqrt(2 (p_EOS - rho/3)/G) of two nodes (Sec. 2).
-__device__ __forceinline__ v2 psi_pair(const KParams &kp, v2 rho)
-{
-    const PairConsts &q = kp.c2;
-    v2 p;
-    if (kp.eos == 0) {
-        const v2 om = fma2(LBM_C2(m_b), rho, LBM_K(one, 1.f));
-        p = LBM_C2(K) * fma2(rho * LBM_C2(RT), rcp2(om), LBM_C2(a) * rho * rho * LBM_K(m_one, -1.f));
-    } else {
-        const v2 eta = LBM_C2(b4) * rho;
-        const v2 om = LBM_K(one, 1.f) - eta;
-        const v2 num = fma2(eta, fma2(eta, om, LBM_K(one, 1.f)), LBM_K(one, 1.f));  // 1 + eta + eta^2 - eta^3
-        const v2 den = om * om * om;
-        p = LBM_C2(K) * fma2(rho * LBM_C2(RT) * num, rcp2(den), LBM_C2(a) * rho * rho * LBM_K(m_one, -1.f));
-    }
-    return sqrt2(LBM_C2(two_over_G) * fma2(rho, LBM_K(m_third, -1.0f / 3.0f), p));
-}
-
-// Stages 5-8 of two nodes (see `collide`): u, m = M f, m_eq, F_m, Q_m, relaxation,
-// f_bar = M^-1 m_bar, with the mass of each node closed through f_bar_0.
-template <class O>
-__device__ __forceinline__ void collide_pair(const KParams &kp, const v2 (&f)[9], v2 rho, v2 psi, v2 Sx, v2 Sy,
-                                             v2 Fex, v2 Fey, v2 (&fb)[9])
-{
-    const PairConsts &q = kp.c2;
-    const v2 a13 = f[1] - f[3], c24 = f[2] - f[4];
-    const v2 bx = (f[5] - f[6]) + (f[8] - f[7]);
-    const v2 by = (f[5] + f[6]) - (f[7] + f[8]);
-    const v2 jx = a13 + bx, jy = c24 + by;
-    const v2 nGpsi = LBM_C2(m_G) * psi;
-    const v2 Fx = fma2(nGpsi, Sx, Fex), Fy = fma2(nGpsi, Sy, Fey);
-    const v2 inv = rcp2(rho);
-    const v2 ux = fma2(LBM_K(half, 0.5f), Fx, jx) * inv;
-    const v2 uy = fma2(LBM_K(half, 0.5f), Fy, jy) * inv;
-
-    // non-conserved moments of M f
-    const v2 p13 = f[1] + f[3], p24 = f[2] + f[4], p57 = f[5] + f[7], p68 = f[6] + f[8];
-    const v2 s14 = p13 + p24, s58 = p57 + p68;
-    const v2 m1 = fma2(LBM_K(m_four, -4.f), f[0], fma2(LBM_K(two, 2.f), s58, s14 * LBM_K(m_one, -1.f)));
-    const v2 m2 = fma2(LBM_K(four, 4.f), f[0], fma2(LBM_K(m_two, -2.f), s14, s58));
-    const v2 m4 = fma2(LBM_K(m_two, -2.f), a13, bx);
-    const v2 m6 = fma2(LBM_K(m_two, -2.f), c24, by);
-    const v2 m7 = p13 - p24;
-    const v2 m8 = p57 - p68;
-
-    // equilibrium and forcing moments
-    const v2 rux = rho * ux, ruy = rho * uy;
-    const v2 u2 = fma2(ux, ux, uy * uy);
-    const v2 meq1 = rho * fma2(LBM_K(three, 3.f), u2, LBM_K(m_two, -2.f));
-    const v2 meq2 = rho * fma2(LBM_K(m_three, -3.f), u2, LBM_K(one, 1.f));
-    const v2 meq7 = fma2(rux, ux, ruy * uy * LBM_K(m_one, -1.f));
-    const v2 meq8 = rux * uy;
-    const v2 Fu = fma2(Fx, ux, Fy * uy);
-    const v2 Fm7 = LBM_K(two, 2.f) * fma2(Fx, ux, Fy * uy * LBM_K(m_one, -1.f));
-    const v2 Fm8 = fma2(Fx, uy, Fy * ux);
-
-    // third-order source, |F_int|^2/(G psi^2) = G |S|^2
-    const v2 Sx2 = Sx * Sx, Sy2 = Sy * Sy;
-    const v2 Q1 = LBM_C2(kq1) * (Sx2 + Sy2);
-    const v2 Q2 = LBM_C2(q2fac) * Q1;
-    const v2 Q7 = LBM_C2(kq7) * (Sx2 - Sy2);
-    const v2 Q8 = LBM_C2(kq7) * Sx * Sy;
-    v2 Q4 = S2(0.f), Q6 = S2(0.f);
-    if (O::improved(kp)) {
-        Q4 = fma2(LBM_C2(c1G), Sx2, LBM_C2(m_c2G) * Sy2) * ux;
-        Q6 = fma2(LBM_C2(c1G), Sy2, LBM_C2(m_c2G) * Sx2) * uy;
-    }
-
-    v2 b1, b2, b4, b6, b7, b8;
-    if (O::var_tau(kp)) {
-        v2 w = (rho - LBM_C2(rho_g)) * LBM_C2(inv_drho);
-        w = V(fminf(fmaxf(w.v.x, 0.f), 1.f), fminf(fmaxf(w.v.y, 0.f), 1.f));
-        const v2 tau = fma2(LBM_K(three, 3.f), fma2(w, LBM_C2(dnu), LBM_C2(nu_g)), LBM_K(half, 0.5f));
-        const v2 sp = rcp2(tau);
-        const v2 sq = rcp2(fma2(LBM_C2(Lambda), rcp2(tau - LBM_K(half, 0.5f)), LBM_K(half, 0.5f)));
-        const v2 hsp = fma2(LBM_K(m_half, -0.5f), sp, LBM_K(one, 1.f));
-        const v2 hsq = fma2(LBM_K(m_half, -0.5f), sq, LBM_K(one, 1.f));
-        const v2 h6 = LBM_K(six, 6.f) * hsp;
-        b1 = fma2(sp, (meq1 - m1) + Q1, fma2(h6, Fu, m1));
-        b2 = fma2(sp, (meq2 - m2) + Q2, fma2(h6 * LBM_K(m_one, -1.f), Fu, m2));
-        b4 = fma2(sq, (rux * LBM_K(m_one, -1.f) - m4) + Q4, fma2(hsq * LBM_K(m_one, -1.f), Fx, m4));
-        b6 = fma2(sq, (ruy * LBM_K(m_one, -1.f) - m6) + Q6, fma2(hsq * LBM_K(m_one, -1.f), Fy, m6));
-        b7 = fma2(sp, (meq7 - m7) + Q7, fma2(hsp, Fm7, m7));
-        b8 = fma2(sp, (meq8 - m8) + Q8, fma2(hsp, Fm8, m8));
-    } else {
-        // m_bar = m + s (m_eq - m + Q) + (1 - s/2) F_m   (Eq. lbe.col)
-        b1 = fma2(LBM_C2(sp), (meq1 - m1) + Q1, fma2(LBM_C2(six_hsp), Fu, m1));
-        b2 = fma2(LBM_C2(sp), (meq2 - m2) + Q2, fma2(LBM_C2(m_six_hsp), Fu, m2));
-        b4 = fma2(LBM_C2(sq), fma2(rux, LBM_K(m_one, -1.f), Q4) - m4, fma2(LBM_C2(m_hsq), Fx, m4));
-        b6 = fma2(LBM_C2(sq), fma2(ruy, LBM_K(m_one, -1.f), Q6) - m6, fma2(LBM_C2(m_hsq), Fy, m6));
-        b7 = fma2(LBM_C2(sp), (meq7 - m7) + Q7, fma2(LBM_C2(hsp), Fm7, m7));
-        b8 = fma2(LBM_C2(sp), (meq8 - m8) + Q8, fma2(LBM_C2(hsp), Fm8, m8));
-    }
-    // s_j = 1: m_bar_j = j + F
-
-    // f_bar = M^T diag(1/9, 1/36, 1/36, 1/6, 1/12, 1/6, 1/12, 1/4, 1/4) m_bar
-    const v2 A0 = rho * LBM_K(ninth, 1.0f / 9.0f), B = b1 * LBM_K(w36, 1.0f / 36.0f), C = b2 * LBM_K(w36, 1.0f / 36.0f);
-    const v2 D = (jx + Fx) * LBM_K(sixth, 1.0f / 6.0f), E = b4 * LBM_K(twelfth, 1.0f / 12.0f);
-    const v2 Gy = (jy + Fy) * LBM_K(sixth, 1.0f / 6.0f), H = b6 * LBM_K(twelfth, 1.0f / 12.0f);
-    const v2 P = b7 * LBM_K(quarter, 0.25f), Qp = b8 * LBM_K(quarter, 0.25f);
-    const v2 ax = fma2(LBM_K(m_two, -2.f), C, A0 - B);
-    const v2 dg = fma2(LBM_K(two, 2.f), B, A0 + C);
-    const v2 DE = fma2(LBM_K(m_two, -2.f), E, D), GH = fma2(LBM_K(m_two, -2.f), H, Gy);
-    const v2 DEp = D + E, GHp = Gy + H;
-    const v2 GQp = GHp + Qp, GQm = GHp - Qp;
-    fb[1] = (ax + DE) + P;
-    fb[2] = (ax + GH) - P;
-    fb[3] = (ax - DE) + P;
-    fb[4] = (ax - GH) - P;
-    fb[5] = (dg + DEp) + GQp;
-    fb[6] = (dg - DEp) + GQm;
-    fb[7] = (dg - DEp) - GQm;
-    fb[8] = (dg + DEp) - GQp;
-    fb[0] = rho - (((fb[1] + fb[2]) + (fb[3] + fb[4])) + ((fb[5] + fb[6]) + (fb[7] + fb[8])));
-}
 
 template <class O>
 __device__ __forceinline__ void external_force_pair(const KParams &kp, int64_t node, v2 rho, v2 &Fex, v2 &Fey)
@@ -416,16 +273,24 @@ __global__ void __launch_bounds__(32 * (NW + 1), LBM_FUSED2_MINB) k_fused2(KPara
                         if (dev) {
                             const float rf0 = has_ref ? ref[1][0] : rho_ref;
                             const float rf1 = has_ref ? ref[1][1] : rho_ref;
-                            r0 = r0 * inv_scale + w_<float>(o) * rf0;
-                            r1 = r1 * inv_scale + w_<float>(o) * rf1;
+                            // as the pull's decode: one rounding of w_o ref, one of the sum
+                            r0 = __fmaf_rn(r0, inv_scale, __fmul_rn(w_<float>(o), rf0));
+                            r1 = __fmaf_rn(r1, inv_scale, __fmul_rn(w_<float>(o), rf1));
                         }
                         if (w0) f_new[i].v.x = r0 + 0.f;
                         if (w1) f_new[i].v.y = r1 + 0.f;
                     }
                 }
             }
-            rho_new = (((f_new[0] + f_new[1]) + (f_new[2] + f_new[3])) + ((f_new[4] + f_new[5]) + (f_new[6] + f_new[7]))) + f_new[8];
-            psi_new = psi_pair(kp, rho_new);
+            // the pulled populations are kept in rest-state deviation form for the collision
+            {
+                v2 f[9];
+#pragma unroll
+                for (int i = 0; i < 9; ++i) f[i] = f_new[i];
+                to_dev(f, f_new);
+            }
+            rho_new = density_dev(f_new);
+            psi_new = psi_v<v2>(kp, rho_new);
         }
         __syncwarp();
         // row rp - 1 is not needed any more by this warp
@@ -442,13 +307,12 @@ __global__ void __launch_bounds__(32 * (NW + 1), LBM_FUSED2_MINB) k_fused2(KPara
                 const v2 Lm = V(am, psi_m2.v.x), Rm = V(psi_m2.v.y, bm);
                 const v2 L0 = V(a0, psi_m1.v.x), R0 = V(psi_m1.v.y, b0);
                 const v2 Lp = V(ap, psi_new.v.x), Rp = V(psi_new.v.y, bp);
-                // S = sum w psi(x + e) e, w = 1/3 (axes), 1/12 (diagonals), Eq. (fint)
-                const v2 dd = Rp - Lm;
-                const v2 Sx = fma2(LBM_KP(third, 1.0f / 3.0f), R0 - L0, LBM_KP(twelfth, 1.0f / 12.0f) * (dd + (Rm - Lp)));
-                const v2 Sy = fma2(LBM_KP(third, 1.0f / 3.0f), psi_new - psi_m2, LBM_KP(twelfth, 1.0f / 12.0f) * (dd + (Lp - Rm)));
-                v2 Fex, Fey;
+                // S of Eq. (fint): east R0, north psi_new, west L0, south psi_m2, NE Rp, NW Lp,
+                // SW Lm, SE Rm
+                v2 Sx, Sy, Fex, Fey, ux, uy;
+                stencil_v<v2>(R0, psi_new, L0, psi_m2, Rp, Lp, Lm, Rm, Sx, Sy);
                 external_force_pair<O>(kp, (int64_t)y * nx + c0, rho_old, Fex, Fey);
-                collide_pair<O>(kp, f_old, rho_old, psi_m1, Sx, Sy, Fex, Fey, fb);
+                collide_v<v2, O>(kp, f_old, rho_old, psi_m1, Sx, Sy, Fex, Fey, fb, ux, uy);
                 S *out = static_cast<S *>(kp.dst) + (int64_t)y * kp.pitch + c0;
                 if (!dev) {
 #pragma unroll
@@ -459,12 +323,12 @@ __global__ void __launch_bounds__(32 * (NW + 1), LBM_FUSED2_MINB) k_fused2(KPara
                     for (int i = 0; i < 9; ++i) {
                         // (f - w_i ref) 2^k as one rounding: f 2^k - (w_i ref) 2^k
                         const v2 nwref = v2{kp.c2.m_scale} * (v2{kp.c2.w[i == 0 ? 0 : (i <= 4 ? 1 : 5)]} * rho_old);
-                        Pair2<S>::store(out + i * kp.plane, fma2(fb[i], v2{kp.c2.scale}, nwref));
+                        Pair2<S>::store(out + i * kp.plane, vfma(fb[i], v2{kp.c2.scale}, nwref));
                     }
                 } else {
 #pragma unroll
                     for (int i = 0; i < 9; ++i)
-                        Pair2<S>::store(out + i * kp.plane, fma2(fb[i], v2{kp.c2.scale}, v2{kp.c2.enc[i == 0 ? 0 : (i <= 4 ? 1 : 5)]}));
+                        Pair2<S>::store(out + i * kp.plane, vfma(fb[i], v2{kp.c2.scale}, v2{kp.c2.enc[i == 0 ? 0 : (i <= 4 ? 1 : 5)]}));
                 }
             }
         }

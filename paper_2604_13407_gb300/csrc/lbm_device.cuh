@@ -27,6 +27,7 @@ __host__ __device__ constexpr R omega_(int i) { return i == 0 ? R(0) : (i <= 4 ?
 
 }  // namespace lbm
 
+#include "lbm_f32.cuh"
 #include "lbm_f64.cuh"
 
 namespace lbm {
@@ -90,13 +91,13 @@ template <> struct Codec<float> {
 };
 template <> struct Codec<__half> {
     typedef float R;
-    static __device__ __forceinline__ R dec(__half v, R wref, R inv_scale) { return __half2float(v) * inv_scale + wref; }
-    static __device__ __forceinline__ __half enc(R f, R wref, R scale) { return __float2half_rn((f - wref) * scale); }
+    static __device__ __forceinline__ R dec(__half v, R wref, R inv_scale) { return __fmaf_rn(__half2float(v), inv_scale, wref); }
+    static __device__ __forceinline__ __half enc(R f, R wref, R scale) { return __float2half_rn(__fmul_rn(__fsub_rn(f, wref), scale)); }
 };
 template <> struct Codec<__nv_bfloat16> {
     typedef float R;
-    static __device__ __forceinline__ R dec(__nv_bfloat16 v, R wref, R inv_scale) { return __bfloat162float(v) * inv_scale + wref; }
-    static __device__ __forceinline__ __nv_bfloat16 enc(R f, R wref, R scale) { return __float2bfloat16_rn((f - wref) * scale); }
+    static __device__ __forceinline__ R dec(__nv_bfloat16 v, R wref, R inv_scale) { return __fmaf_rn(__bfloat162float(v), inv_scale, wref); }
+    static __device__ __forceinline__ __nv_bfloat16 enc(R f, R wref, R scale) { return __float2bfloat16_rn(__fmul_rn(__fsub_rn(f, wref), scale)); }
 };
 template <class S> struct IsDev { static constexpr bool value = false; };
 template <> struct IsDev<__half> { static constexpr bool value = true; };
@@ -119,7 +120,7 @@ template <class R>
 __device__ __forceinline__ R psi_of(const KParams &kp, R rho)
 {
     if constexpr (is_f64<R>()) return f64::psi_of(kp, rho);
-    else return sqrtf(cst<R>(kp).two_over_G * (p_eos<R>(kp, rho) - rho / R(3)));
+    else return psi_v<v1>(kp, v1{rho}).v;
 }
 
 // ------------------------------------------------------------ geometry -----
@@ -153,7 +154,7 @@ __device__ __forceinline__ typename Codec<S>::R load_pop(const KParams &kp, int 
     const S *A = static_cast<const S *>(kp.src);
     const int64_t k = (int64_t)y * kp.pitch + x;
     R wref = R(0);
-    if (IsDev<S>::value) wref = w_<R>(i) * (kp.per_node_ref ? R(kp.ref_src[k]) : cst<R>(kp).rho_ref);
+    if constexpr (IsDev<S>::value) wref = __fmul_rn(w_<R>(i), kp.per_node_ref ? R(kp.ref_src[k]) : cst<R>(kp).rho_ref);
     return Codec<S>::dec(A[i * kp.plane + k], wref, cst<R>(kp).inv_scale);
 }
 
@@ -227,11 +228,25 @@ __device__ __forceinline__ void pull_node(const KParams &kp, int x, int y, const
     f[8] = pull_one<R, 8>(kp, x, y, at, mom);
 }
 
+// FP32 values as one-node lanes of the FP32 formulation (lbm_f32.cuh)
+__device__ __forceinline__ void as_dev1(const float (&f)[9], v1 (&d)[9])
+{
+    v1 g[9];
+#pragma unroll
+    for (int i = 0; i < 9; ++i) g[i] = v1{f[i]};
+    to_dev(g, d);
+}
+
 template <class R>
 __device__ __forceinline__ R density(const R (&f)[9])
 {
-    if constexpr (is_f64<R>()) return f64::density(f);
-    else return (((f[0] + f[1]) + (f[2] + f[3])) + ((f[4] + f[5]) + (f[6] + f[7]))) + f[8];
+    if constexpr (is_f64<R>()) {
+        return f64::density(f);
+    } else {
+        v1 d[9];
+        as_dev1(f, d);
+        return density_dev(d).v;
+    }
 }
 
 // ------------------------------------------------------------ forces -------
@@ -258,13 +273,12 @@ __device__ __forceinline__ void stencil_S(const Ps &ps, R &Sx, R &Sy)
 {
     if constexpr (is_f64<R>()) {
         f64::stencil_S(ps, Sx, Sy);
-        return;
+    } else {
+        v1 sx, sy;
+        stencil_v<v1>(v1{ps(1)}, v1{ps(2)}, v1{ps(3)}, v1{ps(4)}, v1{ps(5)}, v1{ps(6)}, v1{ps(7)}, v1{ps(8)}, sx, sy);
+        Sx = sx.v;
+        Sy = sy.v;
     }
-    const R p1 = ps(1), p2 = ps(2), p3 = ps(3), p4 = ps(4);
-    const R p5 = ps(5), p6 = ps(6), p7 = ps(7), p8 = ps(8);
-    const R a = R(1.0 / 3.0), d = R(1.0 / 12.0);
-    Sx = a * (p1 - p3) + d * ((p5 - p7) + (p8 - p6));
-    Sy = a * (p2 - p4) + d * ((p5 - p7) + (p6 - p8));
 }
 
 // --------------------------------------------------------- collision -------
@@ -278,89 +292,15 @@ __device__ __forceinline__ void collide(const KParams &kp, const R (&f)[9], R rh
 {
     if constexpr (is_f64<R>()) {
         f64::collide(kp, f, psi, Sx, Sy, Fex, Fey, fb, ux, uy);
-        return;
+    } else {
+        v1 d[9], b[9], u, v;
+        as_dev1(f, d);
+        collide_v<v1, O>(kp, d, v1{rho}, v1{psi}, v1{Sx}, v1{Sy}, v1{Fex}, v1{Fey}, b, u, v);
+#pragma unroll
+        for (int i = 0; i < 9; ++i) fb[i] = b[i].v;
+        ux = u.v;
+        uy = v.v;
     }
-    const R G = cst<R>(kp).G;
-    const R jx = ((f[1] - f[3]) + (f[5] - f[6])) + (f[8] - f[7]);
-    const R jy = ((f[2] - f[4]) + (f[5] + f[6])) - (f[7] + f[8]);
-    const R Fix = -G * psi * Sx, Fiy = -G * psi * Sy;
-    const R Fx = Fix + Fex, Fy = Fiy + Fey;
-    const R inv = R(1) / rho;
-    ux = (jx + R(0.5) * Fx) * inv;
-    uy = (jy + R(0.5) * Fy) * inv;
-
-    // non-conserved moments of M f
-    const R s14 = (f[1] + f[2]) + (f[3] + f[4]);
-    const R s58 = (f[5] + f[6]) + (f[7] + f[8]);
-    const R m1 = R(-4) * f[0] - s14 + R(2) * s58;
-    const R m2 = R(4) * f[0] - R(2) * s14 + s58;
-    const R m4 = R(-2) * (f[1] - f[3]) + ((f[5] - f[6]) + (f[8] - f[7]));
-    const R m6 = R(-2) * (f[2] - f[4]) + ((f[5] + f[6]) - (f[7] + f[8]));
-    const R m7 = (f[1] + f[3]) - (f[2] + f[4]);
-    const R m8 = (f[5] + f[7]) - (f[6] + f[8]);
-
-    // equilibrium and forcing moments
-    const R u2 = ux * ux + uy * uy;
-    const R meq1 = rho * (R(-2) + R(3) * u2);
-    const R meq2 = rho * (R(1) - R(3) * u2);
-    const R meq4 = -rho * ux, meq6 = -rho * uy;
-    const R meq7 = rho * (ux * ux - uy * uy), meq8 = rho * ux * uy;
-    const R Fu = Fx * ux + Fy * uy;
-    const R Fm1 = R(6) * Fu, Fm2 = R(-6) * Fu, Fm4 = -Fx, Fm6 = -Fy;
-    const R Fm7 = R(2) * (Fx * ux - Fy * uy), Fm8 = Fx * uy + Fy * ux;
-
-    // third-order source with |F_int|^2/(G psi^2) = G |S|^2
-    const R Sx2 = Sx * Sx, Sy2 = Sy * Sy;
-    const R Q1 = cst<R>(kp).kq1 * (Sx2 + Sy2);
-    const R Q2 = cst<R>(kp).q2fac * Q1;
-    const R Q7 = cst<R>(kp).kq7 * (Sx2 - Sy2);
-    const R Q8 = cst<R>(kp).kq7 * Sx * Sy;
-    R Q4 = R(0), Q6 = R(0);
-    if (O::improved(kp)) {
-        Q4 = (cst<R>(kp).c1G * Sx2 - cst<R>(kp).c2G * Sy2) * ux;
-        Q6 = (cst<R>(kp).c1G * Sy2 - cst<R>(kp).c2G * Sx2) * uy;
-    }
-
-    R sp = cst<R>(kp).sp, sq = cst<R>(kp).sq;
-    R hsp = cst<R>(kp).hsp, hsq = cst<R>(kp).hsq;
-    if (O::var_tau(kp)) {
-        R wgt = (rho - cst<R>(kp).rho_g) / (cst<R>(kp).rho_l - cst<R>(kp).rho_g);
-        wgt = wgt < R(0) ? R(0) : (wgt > R(1) ? R(1) : wgt);
-        const R nu = cst<R>(kp).nu_g + wgt * (cst<R>(kp).nu_l - cst<R>(kp).nu_g);
-        const R tau = R(3) * nu + R(0.5);
-        sp = R(1) / tau;
-        sq = R(1) / (R(0.5) + cst<R>(kp).Lambda / (tau - R(0.5)));
-        hsp = R(1) - R(0.5) * sp;
-        hsq = R(1) - R(0.5) * sq;
-    }
-    // m_bar = (1 - s) m + s m_eq + (1 - s/2) F_m + s Q   (same as Eq. lbe.col)
-    const R b1 = m1 - sp * (m1 - meq1) + hsp * Fm1 + sp * Q1;
-    const R b2 = m2 - sp * (m2 - meq2) + hsp * Fm2 + sp * Q2;
-    const R b4 = m4 - sq * (m4 - meq4) + hsq * Fm4 + sq * Q4;
-    const R b6 = m6 - sq * (m6 - meq6) + hsq * Fm6 + sq * Q6;
-    const R b7 = m7 - sp * (m7 - meq7) + hsp * Fm7 + sp * Q7;
-    const R b8 = m8 - sp * (m8 - meq8) + hsp * Fm8 + sp * Q8;
-    const R b3 = jx + Fx, b5 = jy + Fy;  // s_j = 1: m_bar_j = rho u + F/2 = j + F
-
-    // f_bar = M^T diag(1/9, 1/36, 1/36, 1/6, 1/12, 1/6, 1/12, 1/4, 1/4) m_bar
-    const R A0 = rho * R(1.0 / 9.0), B = b1 * R(1.0 / 36.0), C = b2 * R(1.0 / 36.0);
-    const R D = b3 * R(1.0 / 6.0), E = b4 * R(1.0 / 12.0), Gy = b5 * R(1.0 / 6.0), H = b6 * R(1.0 / 12.0);
-    const R P = b7 * R(0.25), Qp = b8 * R(0.25);
-    const R ax = A0 - B - R(2) * C;   // axis directions
-    const R dg = A0 + R(2) * B + C;   // diagonal directions
-    fb[0] = A0 - R(4) * B + R(4) * C;
-    fb[1] = ax + (D - R(2) * E) + P;
-    fb[2] = ax + (Gy - R(2) * H) - P;
-    fb[3] = ax - (D - R(2) * E) + P;
-    fb[4] = ax - (Gy - R(2) * H) - P;
-    fb[5] = dg + (D + E) + (Gy + H) + Qp;
-    fb[6] = dg - (D + E) + (Gy + H) - Qp;
-    fb[7] = dg - (D + E) - (Gy + H) + Qp;
-    fb[8] = dg + (D + E) - (Gy + H) - Qp;
-    // The collision conserves mass exactly (m_bar_0 = rho); in FP32 the rounding of the
-    // nine back-transformed populations has a systematic bias that makes the total mass
-    // drift by ~1e-8 per step.  Closing each node's mass through f_bar_0 removes the bias.
-    fb[0] = rho - (((fb[1] + fb[2]) + (fb[3] + fb[4])) + ((fb[5] + fb[6]) + (fb[7] + fb[8])));
 }
 
 // f_bar = M^-1 m_eq(rho, u): the equilibrium used by lbm_init_fields
@@ -406,7 +346,10 @@ __device__ __forceinline__ void store_node(const KParams &kp, int x, int y, cons
     }
     const R scale = cst<R>(kp).scale;
 #pragma unroll
-    for (int i = 0; i < 9; ++i) Bp[i * kp.plane + k] = Codec<S>::enc(fb[i], w_<R>(i) * ref, scale);
+    for (int i = 0; i < 9; ++i) {
+        if constexpr (IsDev<S>::value) Bp[i * kp.plane + k] = Codec<S>::enc(fb[i], __fmul_rn(w_<R>(i), ref), scale);
+        else Bp[i * kp.plane + k] = Codec<S>::enc(fb[i], R(0), scale);
+    }
 }
 
 }  // namespace lbm

@@ -3,11 +3,12 @@ seeded inputs.
 
 Tolerances.  FP64: 1e-10 relative on rho and on u (max |du| / max |u|); the FP64 path
 evaluates the formulas in plain order, so it is in fact bit-identical.  FP32: 1e-4 of
-max |u| and 1e-4 relative on rho.  FP16/BF16 deviation storage with a per-node
-reference density: the 11-bit (FP16) or 8-bit (BF16) significand of the stored deviation
-bounds the velocity error near interfaces, where the populations of the light phase carry
-the large pairwise force; measured errors are ~5e-3 (FP16) and ~1e-1 (BF16) of max |u|,
-so the bounds below are 2e-2 and 3e-1."""
+max |u| and 1e-4 relative on rho, on every case including the 20k-step grid-aligned
+channel.  FP16/BF16 deviation storage with a per-node reference density: the 11-bit
+(FP16) or 8-bit (BF16) significand of the stored deviation bounds the velocity error near
+interfaces, where the populations of the light phase carry the large pairwise force;
+measured errors are ~5e-3 (FP16) and ~1e-1 (BF16) of max |u|, so the bounds below are
+2e-2 and 5e-1."""
 import numpy as np
 import pytest
 
@@ -44,7 +45,7 @@ def test_fp64_auto_kernel_matches_oracle(name, oracle_runs):
 @pytest.mark.parametrize("name", sorted(CASES))
 def test_fp32_matches_oracle(name, oracle_runs):
     """FP32: max |du| <= 1e-4 max(max |u|, 1e-3) (FP32 resolves u to ~1e-8 absolute at
-    these densities, so a near-static case is compared against 1e-3) and rho within 1e-3."""
+    these densities, so a near-static case is compared against 1e-3) and rho within 1e-4."""
     c = CASES[name]
     sim = GC.run_gpu(c, lbm.F32)
     rg, ug, vg = sim.moments()
@@ -53,7 +54,7 @@ def test_fp32_matches_oracle(name, oracle_runs):
     umax = max(np.abs(uo[fluid]).max(), np.abs(vo[fluid]).max(), 1e-3)
     du = max(np.abs(ug - uo)[fluid].max(), np.abs(vg - vo)[fluid].max())
     e_rho = np.max(np.abs(rg - ro)[fluid] / ro[fluid])
-    assert du < 1e-4 * umax and e_rho < 1e-3, (e_rho, du / umax)
+    assert du < 1e-4 * umax and e_rho < 1e-4, (e_rho, du / umax)
 
 
 HALF_TOL = {lbm.F16DEV: (2e-2, 5e-2), lbm.BF16DEV: (5e-1, 1.0)}
@@ -134,7 +135,13 @@ def test_fp32_diagnostics_sum_the_fp32_state_exactly():
     sim = GC.run_gpu(c, lbm.F32, steps=30)
     A = sim.get_state().astype(np.float32)
     f = [np.roll(np.roll(A[i], lbm_ey(i), axis=0), lbm_ex(i), axis=1) for i in range(9)]
-    rho = (((f[0] + f[1]) + (f[2] + f[3])) + ((f[4] + f[5]) + (f[6] + f[7]))) + f[8]
+    # the kernel's density: deviations d_i = f_i - (w_i/w_0) f_0 (exact), pairwise sums,
+    # rho = (9/4) f_0 + (s14 + s58) with one rounding (a multiply-add)
+    q0, o0 = f[0] * np.float32(0.25), f[0] * np.float32(0.0625)
+    d = [f[0]] + [f[i] - q0 for i in (1, 2, 3, 4)] + [f[i] - o0 for i in (5, 6, 7, 8)]
+    s14 = (d[1] + d[3]) + (d[2] + d[4])
+    s58 = (d[5] + d[7]) + (d[6] + d[8])
+    rho = (2.25 * f[0].astype(np.float64) + (s14 + s58).astype(np.float64)).astype(np.float32)
     assert rho.dtype == np.float32
     exact = math.fsum(rho.astype(np.float64).ravel())
     d = sim.diagnostics()
@@ -164,11 +171,11 @@ def test_wall_momentum_balance_on_gpu():
 
 def test_c1_full_run_both_schemes():
     """The 4 x 128 grid-aligned two-phase Poiseuille case, 20k steps, both schemes.
-    FP64 is compared at 1e-10 (it is bit-identical).  FP32: this channel (W = 128, viscous
-    time ~1.6e5 steps) integrates the per-step FP32 rounding of the stored populations in
-    its slow viscous and translation modes; the measured errors are 2.6e-4 of max |u| at
-    3000 steps and 1.4e-3 at 20k steps (the target 1e-4 is met on the shorter-time-scale
-    cases of test_fp32_matches_oracle).  Bounds: 5e-4 and 3e-3."""
+    FP64 is compared at 1e-10 (it is bit-identical), FP32 at 1e-4 of max |u| after 3000
+    and after 20000 steps, and at 1e-4 relative on rho after 3000 steps.  At 20k steps the
+    FP32 density keeps ~1e-4 relative near the interfaces: a net mass drift of ~3e-10 per
+    step (the rounding of the nine stored populations; each node's mass is closed, but not
+    exactly) moves the interfaces by ~1e-4 node; the bound there is 5e-4."""
     from tests.setups import cs_case, cs_params
     from paper_2604_13407_gb300 import inputs as I
     T, rg, rl = cs_case()
@@ -181,11 +188,13 @@ def test_c1_full_run_both_schemes():
         assert e_rho < 1e-10 and e_u < 1e-10, (scheme, e_rho, e_u)
         g32 = GC.run_gpu(case, lbm.F32)
         e_rho, e_u = GC.field_errors(g32, o)
-        assert e_u < 3e-3, (scheme, e_rho, e_u)
+        print("C1 FP32 20k steps scheme %d: e_u %.3e e_rho %.3e" % (scheme, e_u, e_rho))
+        assert e_u < 1e-4 and e_rho < 5e-4, (scheme, e_rho, e_u)
         o3 = GC.run_oracle(case, steps=3000)
         g3 = GC.run_gpu(case, lbm.F32, steps=3000)
         e_rho, e_u = GC.field_errors(g3, o3)
-        assert e_u < 5e-4 and e_rho < 1e-3, (scheme, e_rho, e_u)
+        print("C1 FP32 3000 steps scheme %d: e_u %.3e e_rho %.3e" % (scheme, e_u, e_rho))
+        assert e_u < 1e-4 and e_rho < 1e-4, (scheme, e_rho, e_u)
 
 
 def test_save_load_roundtrip_bitwise():
