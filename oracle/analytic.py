@@ -55,9 +55,11 @@ def dpsi(rho, eos, a, b, R, T, K=1.0, G=-1.0):
 
 
 def cs_critical(a, b, R):
-    """Carnahan-Starling critical point with the usual constants T_c = 0.3773 a/(b R),
-    rho_c = 0.1304/b (the form the pseudopotential literature uses)."""
-    return 0.3773 * a / (b * R), 0.1304 / b
+    """Carnahan-Starling critical point with the usual four-digit constants: T_c =
+    0.3773 a/(b R) and the critical packing fraction eta_c = b rho_c/4 = 0.1304, i.e.
+    rho_c = 0.5218/b (0.1304 for the b = 4 of the pseudopotential literature).
+    tests/test_eos_pins.py finds both from the oracle's compiled p_EOS."""
+    return 0.3773 * a / (b * R), 4.0 * 0.1304 / b
 
 
 def vdw_critical(a, b, R):
