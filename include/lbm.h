@@ -147,7 +147,7 @@ LBM_API lbm_status lbm_params_default(lbm_params *p);
 
 /* Validate parameters and allocate a context on the current CUDA device.
  * cuda_stream: a cudaStream_t to run on, or NULL for a stream the library creates.
- * Rejects (LBM_EINVAL): nx or ny < 1, tau <= 1/2, G >= 0, Lambda <= 0,
+ * Rejects (LBM_EINVAL): nx or ny < 1, ny > 65535, tau <= 1/2, G >= 0, Lambda <= 0,
  * p_EOS - rho/3 >= 0 somewhere on (0, rho_max], unknown enum values.
  * The populations are zero until lbm_init_fields or lbm_set_state. */
 LBM_API lbm_status lbm_create(const lbm_params *p, void *cuda_stream, lbm_ctx **out);
@@ -185,8 +185,12 @@ LBM_API lbm_status lbm_set_wall_density(lbm_ctx *ctx, const double *wall_rho);
 LBM_API lbm_status lbm_init_fields(lbm_ctx *ctx, const double *rho, const double *ux, const double *uy,
                            int on_device);
 
-/* Advance nsteps time steps on the context stream.  Returns without waiting for the
- * device unless an error word must be read. */
+/* Advance nsteps time steps on the context stream.  Launches the kernels and returns
+ * without waiting for the device.  A device-side failure of a launched step (a bounded
+ * wait that ran out: LBM_ETIMEOUT; a bounds check: LBM_EBOUNDS) is recorded in a device
+ * error word and reported by the next call that waits for the stream: lbm_sync,
+ * lbm_get_moments / lbm_get_state with host buffers, lbm_get_diagnostics, lbm_save_state
+ * and lbm_adjoint_step. */
 LBM_API lbm_status lbm_step(lbm_ctx *ctx, int64_t nsteps);
 
 /* Density and velocity of the current state (the state the next step pulls), computed
@@ -238,7 +242,8 @@ LBM_API lbm_status lbm_set_param(lbm_ctx *ctx, int32_t which, double value);
 LBM_API lbm_status lbm_adjoint_step(lbm_ctx *ctx, int64_t nsteps, int32_t checkpoint_every,
                             int32_t objective, double *J, double grad[4], double *lambda0);
 
-/* Block until the context stream is idle. */
+/* Block until the context stream is idle; returns the status recorded by the device
+ * error word of the steps launched so far (see lbm_step). */
 LBM_API lbm_status lbm_sync(lbm_ctx *ctx);
 
 /* Number of steps since the last lbm_init_fields / lbm_set_state. */
@@ -262,12 +267,16 @@ LBM_API int32_t lbm_kernel_in_use(const lbm_ctx *ctx);
  * Scratch: the pseudopotential field lives in one file-scope device array of
  * LBM_NOALLOC_MAX_NODES floats (4 MiB) that every device loading the library holds until
  * exit.  The first call on each device looks up that array's device address with that
- * device current; make that first call before any stream capture.  All calls on a device
- * share the array, so calls that overlap on the GPU (other streams, other threads) race:
- * serialise them.  No call reads scratch left by an earlier one.
+ * device current; make that first call before any stream capture.  The address is kept
+ * per device together with the ID of its context: after cudaDeviceReset, or with another
+ * context current, the next call looks it up again (and is then again a first call).
+ * All calls on a device share the array, so calls that overlap on the GPU (other
+ * streams, other threads) race: serialise them.  No call reads scratch left by an
+ * earlier one.
  * Errors (message in lbm_last_error(NULL)): LBM_EINVAL for null or aliasing buffers, a
- * bad struct_size, pitch < nx, or nx * ny > LBM_NOALLOC_MAX_NODES; LBM_ENOTSUP for a
- * precision other than LBM_F32 or LBM_FORCE_FIELD; LBM_ECUDA for a failed launch. */
+ * bad struct_size, pitch < nx, ny > 65535 or nx * ny > LBM_NOALLOC_MAX_NODES;
+ * LBM_ENOTSUP for a precision other than LBM_F32 or LBM_FORCE_FIELD; LBM_ECUDA for a
+ * failed launch. */
 LBM_API lbm_status lbm_step_noalloc_f32(const lbm_params *p, const float *src, float *dst, int64_t pitch,
                                         void *cuda_stream);
 

@@ -215,8 +215,10 @@ __global__ void __launch_bounds__(32 * (NW + 1), LBM_FUSED2_MINB) k_fused2(KPara
             }
         }
         // drain: every issued row must have landed before the CTA may exit
+        bool drained = true;
         for (int q = max(first, r - RING); q < r && q <= last; ++q)
-            mbar_wait_bounded(full + ((q - first) & (RING - 1)), (uint32_t)(((q - first) / RING) & 1));
+            drained &= mbar_wait_bounded(full + ((q - first) & (RING - 1)), (uint32_t)(((q - first) / RING) & 1));
+        if (!drained) atomicOr(kp.err, DERR_TIMEOUT);
         return;
     }
 
@@ -350,16 +352,9 @@ struct Fused2 {
     template <bool P, class O>
     static cudaError_t launch_one(const KParams &kp, cudaStream_t st)
     {
-        static bool configured = false;
-        if (!configured) {
-            cudaError_t e = cudaFuncSetAttribute(k_fused2<S, NW, RING, P, O>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                 (int)L::bytes(true));
-            if (e != cudaSuccess) return e;
-            configured = true;
-        }
-        int dev = 0, sms = 148;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        cudaError_t e = ensure_smem_attribute(k_fused2<S, NW, RING, P, O>, kp.device, (int)L::bytes(true));
+        if (e != cudaSuccess) return e;
+        const int sms = kp.sm_count > 0 ? kp.sm_count : 148;
         const int strips = (kp.nx + L::TX - 1) / L::TX;
         int nseg = (16 * sms + strips - 1) / strips;
         // segments re-read 3 halo rows; a lattice whose two population buffers fit in L2 reads

@@ -267,9 +267,7 @@ struct TwoPass {
     }
     static cudaError_t diag(const KParams &kp, double *acc, unsigned long long *umax, int *nanc, cudaStream_t st)
     {
-        int dev = 0, sms = 148;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        const int sms = kp.sm_count > 0 ? kp.sm_count : 148;
         const int64_t n = (int64_t)kp.nx * kp.ny;
         int64_t blocks = (n + kRowThreads - 1) / kRowThreads;
         if (blocks > 32 * (int64_t)sms) blocks = 32 * (int64_t)sms;

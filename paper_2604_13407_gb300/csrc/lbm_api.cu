@@ -5,6 +5,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <string>
 #include <vector>
@@ -20,6 +21,7 @@ struct lbm_ctx {
     cudaStream_t stream = nullptr;
     bool own_stream = false;
     int device = 0;
+    int sm_count = 0;
     size_t elem = 0;        // bytes per stored population
     size_t real = 0;        // bytes of the arithmetic type (psi field)
     int64_t pitch = 0;      // elements per row of a population plane
@@ -115,6 +117,7 @@ static lbm_status validate(lbm_ctx *c, const lbm_params &p)
     if (p.struct_size != (int32_t)sizeof(lbm_params)) return fail(c, LBM_EINVAL, "lbm_params.struct_size does not match this library");
     if (p.nx < 1 || p.ny < 1) return fail(c, LBM_EINVAL, "nx and ny must be >= 1");
     if ((int64_t)p.nx * p.ny > (int64_t)1 << 31) return fail(c, LBM_EINVAL, "lattice larger than 2^31 nodes");
+    if (p.ny > 65535) return fail(c, LBM_EINVAL, "ny must be <= 65535 (one grid row of blocks per lattice row)");
     if (p.precision < LBM_F64 || p.precision > LBM_BF16DEV) return fail(c, LBM_EINVAL, "unknown precision");
     if (p.scheme != LBM_SCHEME_ORIGINAL && p.scheme != LBM_SCHEME_IMPROVED) return fail(c, LBM_EINVAL, "unknown scheme");
     if (p.eos != LBM_EOS_VDW && p.eos != LBM_EOS_CS) return fail(c, LBM_EINVAL, "unknown eos");
@@ -149,6 +152,8 @@ static void fill_constants(lbm_ctx *c)
     KParams &k = c->kp;
     k.nx = p.nx;
     k.ny = p.ny;
+    k.device = c->device;
+    k.sm_count = c->sm_count;
     k.pitch = c->pitch;
     k.plane = c->plane;
     k.periodic_x = p.periodic_x != 0;
@@ -292,6 +297,11 @@ extern "C" lbm_status lbm_create(const lbm_params *p, void *cuda_stream, lbm_ctx
     if (e != cudaSuccess) {
         delete c;
         return fail(nullptr, LBM_ECUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(e));
+    }
+    e = cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, c->device);
+    if (e != cudaSuccess) {
+        delete c;
+        return fail(nullptr, LBM_ECUDA, std::string("cudaDeviceGetAttribute: ") + cudaGetErrorString(e));
     }
     if (cuda_stream) {
         c->stream = static_cast<cudaStream_t>(cuda_stream);
@@ -486,11 +496,14 @@ static lbm_status run_steps(lbm_ctx *c, int64_t nsteps)
     return LBM_OK;
 }
 
-static lbm_status check_error_word(lbm_ctx *c)
+// Wait for the context stream and read the device error word (set by a bounded device-side
+// wait that ran out, or a failed bounds check, in any step launched so far).  Every call
+// that synchronises anyway reads it: lbm_sync, the host-side getters and lbm_save_state.
+static lbm_status sync_and_check(lbm_ctx *c, const char *what)
 {
     int h = 0;
     CK(cudaMemcpyAsync(&h, c->derr, sizeof(int), cudaMemcpyDeviceToHost, c->stream), "error word");
-    CK(cudaStreamSynchronize(c->stream), "step");
+    CK(cudaStreamSynchronize(c->stream), what);
     if (h & DERR_TIMEOUT) return fail(c, LBM_ETIMEOUT, "a device-side wait ran out of iterations");
     if (h & DERR_BOUNDS) return fail(c, LBM_EBOUNDS, "a device-side bounds check failed");
     return LBM_OK;
@@ -501,10 +514,7 @@ extern "C" lbm_status lbm_step(lbm_ctx *c, int64_t nsteps)
     if (!c) return LBM_EINVAL;
     if (!c->initialised) return fail(c, LBM_ESTATE, "fields not initialised");
     if (nsteps < 0) return fail(c, LBM_EINVAL, "nsteps < 0");
-    lbm_status s = run_steps(c, nsteps);
-    if (s != LBM_OK) return s;
-    if (c->fused_ok) return check_error_word(c);
-    return LBM_OK;
+    return run_steps(c, nsteps);
 }
 
 // psi field of the current state (needed by the moments and diagnostics kernels)
@@ -532,8 +542,7 @@ extern "C" lbm_status lbm_get_moments(lbm_ctx *c, double *rho, double *ux, doubl
     if (rho) CK(cudaMemcpyAsync(rho, d, n * 8, cudaMemcpyDeviceToHost, c->stream), "D2H");
     if (ux) CK(cudaMemcpyAsync(ux, d + n, n * 8, cudaMemcpyDeviceToHost, c->stream), "D2H");
     if (uy) CK(cudaMemcpyAsync(uy, d + 2 * n, n * 8, cudaMemcpyDeviceToHost, c->stream), "D2H");
-    CK(cudaStreamSynchronize(c->stream), "get_moments");
-    return LBM_OK;
+    return sync_and_check(c, "get_moments");
 }
 
 extern "C" lbm_status lbm_get_diagnostics(lbm_ctx *c, double out[LBM_NDIAG])
@@ -548,7 +557,7 @@ extern "C" lbm_status lbm_get_diagnostics(lbm_ctx *c, double out[LBM_NDIAG])
     CK(c->L.diag(c->kp, c->dacc, umax, nanc, c->stream), "diagnostics kernel");
     double h[16];
     CK(cudaMemcpyAsync(h, c->dacc, sizeof h, cudaMemcpyDeviceToHost, c->stream), "D2H");
-    CK(cudaStreamSynchronize(c->stream), "diagnostics");
+    if ((s = sync_and_check(c, "diagnostics")) != LBM_OK) return s;
     for (int k = 0; k < 9; ++k) out[k] = h[k];
     unsigned long long ub;
     std::memcpy(&ub, &h[9], 8);
@@ -574,8 +583,7 @@ extern "C" lbm_status lbm_get_state(lbm_ctx *c, double *pops, int on_device)
     if ((s = need_scratch(c, 9 * n * sizeof(double))) != LBM_OK) return s;
     CK(c->L.get_state(c->kp, c->scratch, c->stream), "get_state kernel");
     CK(cudaMemcpyAsync(pops, c->scratch, 9 * n * 8, cudaMemcpyDeviceToHost, c->stream), "D2H");
-    CK(cudaStreamSynchronize(c->stream), "get_state");
-    return LBM_OK;
+    return sync_and_check(c, "get_state");
 }
 
 extern "C" lbm_status lbm_set_state(lbm_ctx *c, const double *pops, int on_device)
@@ -629,7 +637,8 @@ extern "C" lbm_status lbm_save_state(lbm_ctx *c, void *host_buf, size_t *nbytes)
     char *dst = static_cast<char *>(host_buf) + sizeof h;
     CK(cudaMemcpyAsync(dst, c->pops[c->cur], pop_bytes, cudaMemcpyDeviceToHost, c->stream), "save");
     if (ref_bytes) CK(cudaMemcpyAsync(dst + pop_bytes, c->refp[c->cur], ref_bytes, cudaMemcpyDeviceToHost, c->stream), "save");
-    CK(cudaStreamSynchronize(c->stream), "save");
+    lbm_status s = sync_and_check(c, "save");
+    if (s != LBM_OK) return s;
     *nbytes = need;
     return LBM_OK;
 }
@@ -688,8 +697,7 @@ extern "C" lbm_status lbm_adjoint_step(lbm_ctx *c, int64_t nsteps, int32_t check
 extern "C" lbm_status lbm_sync(lbm_ctx *c)
 {
     if (!c) return LBM_EINVAL;
-    CK(cudaStreamSynchronize(c->stream), "sync");
-    return LBM_OK;
+    return sync_and_check(c, "sync");
 }
 
 extern "C" int64_t lbm_step_count(const lbm_ctx *c) { return c ? c->steps : -1; }
@@ -728,7 +736,7 @@ ContextView view_of(lbm_ctx *c)
     v.collide_pass = c->L.collide_pass;
     v.L = &c->L;
     v.check_error = [](lbm_ctx *cc, std::string &m) {
-        lbm_status s = check_error_word(cc);
+        lbm_status s = sync_and_check(cc, "adjoint");
         if (s != LBM_OK) m = cc->err;
         return s;
     };
@@ -749,11 +757,26 @@ lbm_status kparams_for(const lbm_params *p, int64_t pitch, KParams *out)
     if (s != LBM_OK) return s;
     lbm_ctx tmp;
     tmp.p = *p;
+    if (cudaGetDevice(&tmp.device) != cudaSuccess ||
+        cudaDeviceGetAttribute(&tmp.sm_count, cudaDevAttrMultiProcessorCount, tmp.device) != cudaSuccess)
+        return fail(nullptr, LBM_ECUDA, "cannot query the current device");
     tmp.pitch = pitch;
     tmp.plane = pitch * p->ny;
     fill_constants(&tmp);
     *out = tmp.kp;
     return LBM_OK;
+}
+
+cudaError_t ensure_smem_attribute_ptr(const void *kernel, int device, int bytes)
+{
+    static std::mutex mu;
+    static std::vector<std::pair<const void *, int>> done;
+    std::lock_guard<std::mutex> lock(mu);
+    for (const auto &d : done)
+        if (d.first == kernel && d.second == device) return cudaSuccess;
+    cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e == cudaSuccess) done.emplace_back(kernel, device);
+    return e;
 }
 
 // Record a message for lbm_last_error(NULL).

@@ -32,6 +32,8 @@ struct PairConsts {
 // (host bookkeeping and the FP64 path) and, for kernels, in cd / cf by arithmetic type.
 struct KParams {
     int nx, ny;
+    int device;    // CUDA device of the context
+    int sm_count;  // its multiprocessor count (queried once, at create)
     int64_t pitch;  // elements per row of a population plane (and of the rho_ref plane)
     int64_t plane;  // elements per population plane = pitch * ny
     int periodic_x, periodic_y;
@@ -103,6 +105,15 @@ enum Prec { P_F64 = 0, P_F32 = 1, P_F16 = 2, P_BF16 = 3 };
 
 // Device error word bits
 enum DevErr { DERR_TIMEOUT = 1, DERR_BOUNDS = 2 };
+
+// One-time set-up of a kernel's dynamic shared-memory limit, per kernel and device (an
+// attribute set with one device current does not apply to another); lbm_api.cu.
+cudaError_t ensure_smem_attribute_ptr(const void *kernel, int device, int bytes);
+template <class K>
+inline cudaError_t ensure_smem_attribute(K kernel, int device, int bytes)
+{
+    return ensure_smem_attribute_ptr(reinterpret_cast<const void *>(kernel), device, bytes);
+}
 
 // Launchers, defined in the per-precision translation units (k_f64.cu, k_f32.cu,
 // k_f16.cu).  All run on `st` and return the launch status.

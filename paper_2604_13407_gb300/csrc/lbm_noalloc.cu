@@ -7,6 +7,7 @@
 // memory and keeps its only scratch buffer -- the pseudopotential field read by the
 // collide pass -- in a file-scope device array of fixed size.  Every device that loads the
 // library holds that array (LBM_NOALLOC_MAX_NODES floats) until the process exits.
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <mutex>
@@ -25,10 +26,42 @@ using namespace lbm;
 // psi scratch of the allocation-free step, shared by every call on a device.
 static __device__ __align__(256) float g_noalloc_psi[LBM_NOALLOC_MAX_NODES];
 
-// Device addresses of g_noalloc_psi, looked up once per device (host code cannot use the
-// symbol's name as a device address).
+// Device address of g_noalloc_psi (host code cannot use the symbol's name as a device
+// address), looked up with the device current and cached per device together with the ID
+// of the context it belongs to: a reset device (cudaDeviceReset) or another context made
+// current gets a new ID, and the next call looks the address up again in that context.
+struct NoallocSlot {
+    unsigned long long ctx_id;
+    float *addr;
+};
 static std::mutex g_noalloc_mutex;
-static float *g_noalloc_addr[256];
+static NoallocSlot g_noalloc_slot[256];
+
+typedef CUresult (*PfnCtxGetCurrent)(CUcontext *);
+typedef CUresult (*PfnCtxGetId)(CUcontext, unsigned long long *);
+
+// ID of the calling thread's current context (0: none is current); driver entry points are
+// fetched through the runtime, so the library needs no link to the driver library.
+static lbm_status current_context_id(unsigned long long *id)
+{
+    static PfnCtxGetCurrent get_current = nullptr;
+    static PfnCtxGetId get_id = nullptr;
+    if (!get_current || !get_id) {
+        void *a = nullptr, *b = nullptr;
+        cudaDriverEntryPointQueryResult qa, qb;
+        cudaError_t e = cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &a, 12000, cudaEnableDefault, &qa);
+        if (e == cudaSuccess) e = cudaGetDriverEntryPointByVersion("cuCtxGetId", &b, 12000, cudaEnableDefault, &qb);
+        if (e != cudaSuccess || !a || !b || qa != cudaDriverEntryPointSuccess || qb != cudaDriverEntryPointSuccess)
+            return set_global_error(LBM_ECUDA, "driver entry points cuCtxGetCurrent / cuCtxGetId not available");
+        get_current = reinterpret_cast<PfnCtxGetCurrent>(a);
+        get_id = reinterpret_cast<PfnCtxGetId>(b);
+    }
+    CUcontext ctx = nullptr;
+    if (get_current(&ctx) != CUDA_SUCCESS) return set_global_error(LBM_ECUDA, "cuCtxGetCurrent failed");
+    *id = 0;
+    if (ctx && get_id(ctx, id) != CUDA_SUCCESS) return set_global_error(LBM_ECUDA, "cuCtxGetId failed");
+    return LBM_OK;
+}
 
 static lbm_status noalloc_scratch(float **out)
 {
@@ -37,14 +70,21 @@ static lbm_status noalloc_scratch(float **out)
     if (e != cudaSuccess) return set_global_error(LBM_ECUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(e));
     if (dev < 0 || dev >= 256) return set_global_error(LBM_ENOTSUP, "device ordinal out of range");
     std::lock_guard<std::mutex> lock(g_noalloc_mutex);
-    if (!g_noalloc_addr[dev]) {
+    unsigned long long ctx = 0;
+    lbm_status s = current_context_id(&ctx);
+    if (s != LBM_OK) return s;
+    NoallocSlot &slot = g_noalloc_slot[dev];
+    if (ctx == 0 || ctx != slot.ctx_id || !slot.addr) {
         void *ptr = nullptr;
         e = cudaGetSymbolAddress(&ptr, g_noalloc_psi);
         if (e != cudaSuccess)
             return set_global_error(LBM_ECUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
-        g_noalloc_addr[dev] = static_cast<float *>(ptr);
+        // the look-up made the device's primary context current if none was
+        if ((s = current_context_id(&ctx)) != LBM_OK) return s;
+        slot.ctx_id = ctx;
+        slot.addr = static_cast<float *>(ptr);
     }
-    *out = g_noalloc_addr[dev];
+    *out = slot.addr;
     return LBM_OK;
 }
 
@@ -62,6 +102,7 @@ extern "C" lbm_status lbm_step_noalloc_f32(const lbm_params *p, const float *src
     if ((int64_t)p->nx * p->ny > (int64_t)LBM_NOALLOC_MAX_NODES)
         return set_global_error(LBM_EINVAL, "lattice larger than LBM_NOALLOC_MAX_NODES (" +
                                                 std::to_string((long long)LBM_NOALLOC_MAX_NODES) + " nodes)");
+    if (p->ny > 65535) return set_global_error(LBM_EINVAL, "ny must be <= 65535 (one grid row of blocks per lattice row)");
     if (pitch < p->nx) return set_global_error(LBM_EINVAL, "pitch must be >= nx");
     KParams kp{};
     lbm_status s = kparams_for(p, pitch, &kp);

@@ -40,7 +40,7 @@ def test_struct_layout_matches():
     assert p.k1 == pytest.approx(-1.895 / 16)
 
 
-@pytest.mark.parametrize("field,value", [("nx", 0), ("tau_l", 0.5), ("G", 0.5), ("Lambda", 0.0),
+@pytest.mark.parametrize("field,value", [("nx", 0), ("ny", 65536), ("tau_l", 0.5), ("G", 0.5), ("Lambda", 0.0),
                                          ("precision", 7), ("eos", 3), ("kernel", 9)])
 def test_create_rejects_invalid_parameters(field, value):
     p = lbm.default_params(**{field: value})

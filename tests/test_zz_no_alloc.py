@@ -58,6 +58,9 @@ def test_noalloc_rejects_oversized_and_wrong_precision():
     big = lbm.default_params(nx=2048, ny=1024, precision=lbm.F32)
     st = lib.lbm_step_noalloc_f32(ctypes.byref(big), ctypes.c_void_p(a.data_ptr()), ctypes.c_void_p(b.data_ptr()), 2048, None)
     assert st == 1 and b"LBM_NOALLOC_MAX_NODES" in lib.lbm_last_error(None)
+    tall = lbm.default_params(nx=8, ny=70000, precision=lbm.F32)   # 560k nodes, but ny > 65535
+    st = lib.lbm_step_noalloc_f32(ctypes.byref(tall), ctypes.c_void_p(a.data_ptr()), ctypes.c_void_p(b.data_ptr()), 8, None)
+    assert st == 1 and b"65535" in lib.lbm_last_error(None)
     p64 = lbm.default_params(nx=8, ny=8, precision=lbm.F64)
     st = lib.lbm_step_noalloc_f32(ctypes.byref(p64), ctypes.c_void_p(a.data_ptr()), ctypes.c_void_p(b.data_ptr()), 8, None)
     assert st == 8
