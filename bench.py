@@ -29,10 +29,11 @@ RHO_G, RHO_L = 0.009291723294794338, 0.3581443962580134  # Maxwell densities of 
 T_07 = 0.7 * 0.3773 / 4.0
 TAU = 1.0
 BYTES = {"f64": 144, "f32": 72, "f16dev": 36, "bf16dev": 36}
-# DRAM bytes per lattice update of the packed fused kernel (k_fused2) at 8192 x 8192, from one ncu
-# launch list (dram__bytes_read.sum + dram__bytes_write.sum; profiles/k_fused2_*_spinodal.md).
-# Valid for the kernel as captured; set to None when the kernel changes until it is captured again.
-TRAFFIC_PER_UPDATE = {"f32": 72.6, "f16dev": 36.1}
+# DRAM bytes per lattice update of the packed fused kernel (k_fused2), scaled from one ncu capture
+# (dram__bytes_read.sum + dram__bytes_write.sum of one launch at 4096 x 4096; profiles/k_fused2_*).
+# Valid for the kernel as captured; an entry is removed when the kernel changes until it is captured
+# again (the line then reports traffic null).
+TRAFFIC_PER_UPDATE = {}
 HBM_FALLBACK = 6800.0
 
 
@@ -115,7 +116,7 @@ class ClockSampler:
 
 # -------------------------------------------------------------- GPU legs --
 
-def make_sim(n, precision, scheme=1, kernel=0, per_node_ref=0):
+def make_sim(n, precision, scheme=1, kernel=0, per_node_ref=1):
     import torch
     from paper_2604_13407_gb300 import lbm
     # FP16 deviations stay below 2^-2 (largest FP16 value 65504 = 2^16 - 2^5); the 2^k
@@ -162,28 +163,12 @@ def job_updates(n, steps, world):
     return float(n) * n * steps * world
 
 
-def per_launch_time(sim, launches=20):
-    """Average duration of one step (the dominant kernel when the fused path runs),
-    CUDA events on the stream the library launches on (torch's current stream)."""
-    import torch
-    ts = []
-    for _ in range(launches):
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record()
-        sim.step(1)
-        e1.record()
-        e1.synchronize()
-        ts.append(e0.elapsed_time(e1) / 1e3)
-    return sum(ts) / len(ts)
-
-
-def e2e_glups(n, precision, steps, rho_host):
+def e2e_glups(n, precision, steps, rho_host, per_node_ref=1):
     """Same metric through the public API with host buffers: H2D of the initial density
     (pinned), `steps` steps, D2H of rho, ux, uy; all inside the timed region."""
     import torch
     from paper_2604_13407_gb300 import lbm
-    sim = make_sim(n, precision)
+    sim = make_sim(n, precision, per_node_ref=per_node_ref)
     pinned = torch.from_numpy(rho_host.reshape(-1)).pin_memory()
     out = [torch.empty(n * n, dtype=torch.float64).pin_memory() for _ in range(3)]
     h = pinned.numpy()
@@ -201,19 +186,18 @@ def e2e_glups(n, precision, steps, rho_host):
     return n * n * steps / t / 1e9, 8 * n * n / steps, 3 * 8 * n * n / steps
 
 
-def adjoint_cost(precision, nsteps, checkpoint_every=200):
-    """Adjoint workload: 256 x 1024 channel (walls at x = -1/2 and 255.5, periodic in y),
-    radius-20 droplet at a seed-4 jittered centre near (128, 900), buoyant gravity
-    g = (0, -2e-6), improved scheme.  Times nsteps forward steps and lbm_adjoint_step over
+def adjoint_cost(precision, nsteps, checkpoint_every=200, nx=256, ny=1024, radius=20.0):
+    """Adjoint workload: nx x ny channel (default 256 x 1024; walls at x = -1/2 and nx - 1/2,
+    periodic in y), droplet of the given radius (default 20) at a seed-4 jittered centre near
+    (nx/2, 0.88 ny), buoyant gravity g = (0, -2e-6), improved scheme.  Times nsteps forward steps and lbm_adjoint_step over
     the same nsteps (forward sweep, segment recompute and transposed steps; objective: the
     y force on the walls; buffers already allocated by a first call) with CUDA events;
     returns the per-step times and their ratio."""
     import torch
     from paper_2604_13407_gb300 import inputs as I
     from paper_2604_13407_gb300 import lbm
-    nx, ny = 256, 1024
-    cx, cy = I.jittered_centre(4, 128.0, 900.0)
-    rho = I.droplet(nx, ny, RHO_L, RHO_G, 20.0, cx, cy, periodic_x=False, periodic_y=True)
+    cx, cy = I.jittered_centre(4, nx / 2.0, ny * 900.0 / 1024.0)
+    rho = I.droplet(nx, ny, RHO_L, RHO_G, radius, cx, cy, periodic_x=False, periodic_y=True)
 
     def sim():
         p = lbm.default_params(nx=nx, ny=ny, periodic_x=0, periodic_y=1, precision=precision, scheme=1,
@@ -245,30 +229,86 @@ def adjoint_cost(precision, nsteps, checkpoint_every=200):
     back = out["adjoint"] - out["forward"]
     return {"forward_ms_per_step": out["forward"], "adjoint_ms_per_step": out["adjoint"],
             "ratio": out["adjoint"] / out["forward"], "backward_ms_per_step": back,
-            "backward_ratio": back / out["forward"], "steps": nsteps, "checkpoint_every": checkpoint_every}
+            "backward_ratio": back / out["forward"], "steps": nsteps, "checkpoint_every": checkpoint_every,
+            "lattice": "%dx%d" % (nx, ny)}
 
 
 # ------------------------------------------------------------ CPU legs ----
 
-def oracle_glups(n, seconds_target=10.0, max_steps=50):
-    """The FP64 oracle on an n x n sample of the workload; returns (GLUPS, steps, threads)."""
+ORACLE_SAMPLES = {
+    "spinodal1024": "1024x1024 periodic spinodal (the 8192x8192 workload's recipe), 100 steps, FP64 oracle",
+    "c1": "4x128 grid-aligned two-phase channel (walls in y, F_x = 1e-7, tau 0.8, improved), 20000 steps, FP64 oracle",
+}
+
+
+def oracle_sample(kind, steps=None):
+    """Time the FP64 oracle on one bounded sample in this process; returns a dict."""
     from oracle import oracle as O
-    p = O.Params(nx=n, ny=n, periodic_x=True, periodic_y=True, scheme=1, T=T_07, rho_l=RHO_L,
-                 rho_g=RHO_G, rho_s=RHO_G, tau_l=TAU, tau_g=TAU)
+    if kind == "spinodal1024":
+        n = 1024
+        p = O.Params(nx=n, ny=n, periodic_x=True, periodic_y=True, scheme=1, T=T_07, rho_l=RHO_L,
+                     rho_g=RHO_G, rho_s=RHO_G, tau_l=TAU, tau_g=TAU)
+        rho, steps = workload_rho(n), steps or 100
+    else:
+        from paper_2604_13407_gb300 import inputs as I
+        p = O.Params(nx=4, ny=128, periodic_x=True, periodic_y=False, scheme=1, T=T_07, rho_l=RHO_L,
+                     rho_g=RHO_G, rho_s=RHO_G, tau_l=0.8, tau_g=0.8, Fx=1e-7)
+        rho, steps = I.tanh_slab(4, 128, RHO_L, RHO_G, 64), steps or 20000
     s = O.OracleSim(p)
-    s.init(workload_rho(n))
-    t0 = time.perf_counter()
+    s.init(rho)
     s.step(1)
-    t1 = time.perf_counter() - t0
-    steps = int(max(1, min(max_steps, seconds_target / max(t1, 1e-6))))
     t0 = time.perf_counter()
     s.step(steps)
     t = time.perf_counter() - t0
-    threads = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
-    return n * n * steps / t / 1e9, steps, threads
+    nodes = p.nx * p.ny
+    return {"kind": kind, "glups": nodes * steps / t / 1e9, "seconds": t, "steps": steps, "nodes": nodes,
+            "threads": O.threads()}
+
+
+def oracle_in_process(kind, threads, steps=None):
+    """oracle_sample in a fresh interpreter with OMP_NUM_THREADS = threads (the OpenMP thread
+    count is fixed when the oracle's runtime starts)."""
+    env = dict(os.environ, OMP_NUM_THREADS=str(threads))
+    cmd = [sys.executable, os.path.abspath(__file__), "--oracle-sample", kind]
+    if steps:
+        cmd += ["--steps", str(steps)]
+    r = subprocess.run(cmd, env=env, capture_output=True, text=True, timeout=900)
+    if r.returncode != 0:
+        raise RuntimeError("oracle sample failed: " + r.stderr[-2000:])
+    return json.loads(r.stdout.strip().splitlines()[-1])
+
+
+def host_cores():
+    try:
+        return int(subprocess.run(["nproc"], capture_output=True, text=True).stdout.strip())
+    except Exception:
+        return os.cpu_count() or 1
+
+
+def cpu_baseline_runs():
+    """The CPU baseline: the oracle single-threaded and on every host core, on the spinodal
+    sample and on the 4 x 128 channel."""
+    cores = host_cores()
+    runs = []
+    for kind in ("spinodal1024", "c1"):
+        for th in (1, cores):
+            r = oracle_in_process(kind, th)
+            r["sample"] = ORACLE_SAMPLES[kind]
+            runs.append(r)
+    return cores, runs
+
+
+def workload_config(n, precision, node_ref=1):
+    storage = precision + (" (per-node reference density)" if precision in ("f16dev", "bf16dev") and node_ref else "")
+    return {"workload": "spinodal %dx%d periodic, Carnahan-Starling 0.7Tc, eps 1.895, improved "
+                        "scheme, tau %.1f, %s population storage" % (n, n, TAU, storage),
+            "nx": n, "ny": n, "storage": precision,
+            "l2": "inputs larger than L2 (population buffers %.1f GB each)" % (BYTES[precision] / 2 * n * n / 1e9)}
 
 
 def run_reference(args):
+    """The reference arm: the FP64 oracle (the CPU restatement of the paper's step), on every
+    host core; each step is one step of a 512 x 512 sample of the same workload."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
@@ -283,15 +323,15 @@ def run_reference(args):
     s.step(args.steps)
     t = time.perf_counter() - t0
     v = n * n * args.steps / t / 1e9
-    threads = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    threads = O.threads()
+    cfg = workload_config(args.n, args.precision, args.node_ref)
+    cfg["parallelism"] = "single"
+    sample = "each step: one oracle step of a %dx%d sample of this workload (seed 5), %d host threads" % (n, n, threads)
     line = {"impl": "reference", "metric": "GLUPS", "value": v, "unit": "GLUPS", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic",
-            "config": {"workload": "spinodal %dx%d periodic sample of the 8192x8192 workload "
-                                   "(CS 0.7Tc, eps 1.895, improved scheme)" % (n, n), "nx": n, "ny": n},
-            "cpu_baseline": {"value": v, "unit": "GLUPS", "cores": threads, "kind": "oracle",
-                             "sample": "%dx%d lattice, %d steps" % (n, n, args.steps)},
+            "data": "synthetic", "config": cfg,
+            "cpu_baseline": {"value": v, "unit": "GLUPS", "cores": threads, "kind": "oracle", "sample": sample},
             "e2e": {"value": v, "unit": "GLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
 
@@ -304,6 +344,9 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--n", type=int, default=8192)
     ap.add_argument("--precision", default="f32", choices=["f64", "f32", "f16dev", "bf16dev"])
+    ap.add_argument("--node-ref", type=int, default=1,
+                    help="FP16/BF16 storage: 1 deviations from w_i rho of the writing node (accurate mode), "
+                         "0 from one reference density")
     ap.add_argument("--variants", type=int, default=1, help="also time the other precisions / scheme")
     ap.add_argument("--cpu-baseline", type=int, default=1)
     ap.add_argument("--ref-sample", type=int, default=512)
@@ -311,9 +354,14 @@ def main():
     ap.add_argument("--adjoint", type=int, default=1, help="also time the adjoint against the forward step")
     ap.add_argument("--adjoint-only", type=int, default=0,
                     help="time only the adjoint against the forward step (one JSON line; for profiling)")
+    ap.add_argument("--oracle-sample", default=None, choices=sorted(ORACLE_SAMPLES),
+                    help="(internal) time one CPU-baseline sample of the oracle and print it")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
+    if args.oracle_sample:
+        print(json.dumps(oracle_sample(args.oracle_sample, args.steps if "--steps" in sys.argv else None)))
+        return
     if args.impl == "reference":
         return run_reference(args)
     if args.adjoint_only:
@@ -344,38 +392,46 @@ def main():
     if not dev_uuid.startswith("GPU-"):
         dev_uuid = "GPU-" + dev_uuid
 
-    sim = make_sim(n, prec_id[args.precision])
+    sim = make_sim(n, prec_id[args.precision], per_node_ref=args.node_ref)
     sim.init_fields(rho)
     kernels_per_step = 1 if sim.kernel_in_use == lbm.KERNEL_FUSED else 2
     with ClockSampler(dev_uuid) as clk:
         t = timed_steps(sim, args.steps, args.warmup, dist_on)
     clocks = clk.summary()
-    t_launch = per_launch_time(sim)
     d = sim.diagnostics()
     sim.close()
     updates = job_updates(n, args.steps, world)
     value = updates / t / 1e9
-    bpu = BYTES[args.precision]
-    achieved = bpu * n * n / t_launch / 1e9
+    bpu = BYTES[args.precision] + (8 if args.precision in ("f16dev", "bf16dev") and args.node_ref else 0)
+    # one kernel launch per step on the fused path: the average launch duration is the timed
+    # region divided by the steps (CUDA events on the launching stream)
+    t_launch = t / args.steps / kernels_per_step
+    achieved = bpu * n * n / (t / args.steps) / 1e9
 
     variants = {}
     if args.variants and rank == 0 and not dist_on:
-        for name, prec, scheme, extra in (("f32_original", "f32", 0, {}), ("f16dev", "f16dev", 1, {}),
-                                          ("bf16dev", "bf16dev", 1, {}), ("f16dev_node_ref", "f16dev", 1, {"per_node_ref": 1}),
-                                          ("f64", "f64", 1, {})):
-            if prec == args.precision and scheme == 1 and not extra:
+        for name, prec, scheme, extra in (
+                ("f32_original", "f32", 0, {}),
+                ("f16dev_node_ref", "f16dev", 1, {"per_node_ref": 1}),
+                ("bf16dev_node_ref", "bf16dev", 1, {"per_node_ref": 1}),
+                ("f16dev_global_ref", "f16dev", 1, {}),
+                ("f64", "f64", 1, {})):
+            if prec == args.precision and scheme == 1 and (prec in ("f32", "f64") or
+                                                             extra.get("per_node_ref", 0) == args.node_ref):
                 continue
-            s2 = make_sim(n, prec_id[prec], scheme=scheme, **extra)
+            s2 = make_sim(n, prec_id[prec], scheme=scheme, per_node_ref=extra.get("per_node_ref", 0))
             s2.init_fields(rho)
             k = max(20, args.steps // (4 if prec == "f64" else 1))
             t2 = timed_steps(s2, k, args.warmup, False)
-            tl = per_launch_time(s2, 5)
             b = BYTES[prec] + (8 if extra.get("per_node_ref") else 0)
-            variants[name] = {"GLUPS": n * n * k / t2 / 1e9, "bytes_per_update": b,
-                              "achieved_GBs": b * n * n / tl / 1e9, "frac": b * n * n / tl / 1e9 / hbm,
+            g = n * n * k / t2 / 1e9
+            variants[name] = {"GLUPS": g, "bytes_per_update": b, "achieved_GBs": b * g, "frac": b * g / hbm,
                               "kernel": "fused" if s2.kernel_in_use == lbm.KERNEL_FUSED else "two_pass"}
+            if name == "f16dev_global_ref":
+                variants[name]["note"] = ("deviations from one reference density: not accurate at this density "
+                                          "ratio (O(1) error); bytes and speed only")
             if prec == "f64":
-                # FP64-ALU bound: ncu shows the FP64 pipe 85% busy and DRAM at 1.4% (k_fused_f64 profile)
+                # FP64-ALU bound: ncu shows the FP64 pipe busy and DRAM nearly idle (k_fused_f64 profile)
                 variants[name]["bound"] = "fp64 alu"
             s2.close()
 
@@ -383,36 +439,36 @@ def main():
     if args.adjoint and rank == 0 and not dist_on:
         adjoint = {"workload": "droplet in a 256x1024 channel (radius 20, buoyant g 2e-6, walls in x, periodic y), "
                                "objective: time-averaged y force on the walls, gradient wrt (Fx, Fy, G, T)",
-                   "f32": adjoint_cost(lbm.F32, 2000), "f64": adjoint_cost(lbm.F64, 400)}
+                   "f32": adjoint_cost(lbm.F32, 2000), "f64": adjoint_cost(lbm.F64, 400),
+                   "f32_2048": adjoint_cost(lbm.F32, 200, 50, nx=2048, ny=2048, radius=160.0)}
 
     e2e = None
     if rank == 0 and args.e2e:
-        ev, hb, db = e2e_glups(n, prec_id[args.precision], args.steps, rho)
+        ev, hb, db = e2e_glups(n, prec_id[args.precision], args.steps, rho, args.node_ref)
         e2e = {"value": ev, "unit": "GLUPS", "h2d_bytes_per_step": hb, "d2h_bytes_per_step": db}
     cpu = None
     if args.cpu_baseline and rank == 0 and not dist_on:
-        g, st, threads = oracle_glups(1024)
-        cpu = {"value": g, "unit": "GLUPS", "cores": threads, "kind": "oracle",
-               "sample": "1024x1024 periodic spinodal, %d steps, FP64" % st}
+        cores, runs = cpu_baseline_runs()
+        head = [r for r in runs if r["kind"] == "spinodal1024" and r["threads"] == cores][0]
+        cpu = {"value": head["glups"], "unit": "GLUPS", "cores": head["threads"], "kind": "oracle",
+               "sample": head["sample"] + ", %d threads" % head["threads"], "nproc": cores,
+               "runs": [{"sample": r["sample"], "threads": r["threads"], "GLUPS": r["glups"], "MLUPS": 1e3 * r["glups"],
+                         "seconds": r["seconds"]} for r in runs]}
     if rank == 0:
+        cfg = workload_config(n, args.precision, args.node_ref)
+        cfg["parallelism"] = "replicas" if world > 1 else "single"
         line = {
             "metric": "GLUPS", "value": value, "unit": "GLUPS", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32" if args.precision != "f64" else "f64",
-            "data": "synthetic",
-            "config": {"workload": "spinodal %dx%d periodic, Carnahan-Starling 0.7Tc, eps 1.895, improved "
-                                   "scheme, tau %.1f, %s population storage" % (n, n, TAU, args.precision),
-                       "nx": n, "ny": n, "storage": args.precision,
-                       "l2": "inputs larger than L2 (population buffers %.1f GB each)" % (bpu / 2 * n * n / 1e9),
-                       "parallelism": "replicas" if world > 1 else "single"},
+            "data": "synthetic", "config": cfg,
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                          "frac": achieved / hbm, "peak_kind": peak_kind,
                          "traffic": (TRAFFIC_PER_UPDATE[args.precision] * n * n
-                                     if kernels_per_step == 1 and n == 8192 and TRAFFIC_PER_UPDATE.get(args.precision)
-                                     else None),
-                         "traffic_unit": "bytes per launch (ncu, 8192x8192)",
-                         "bytes_per_update": bpu,
-                         "kernel": "fused" if kernels_per_step == 1 else "two_pass (step)"},
+                                     if kernels_per_step == 1 and TRAFFIC_PER_UPDATE.get(args.precision) else None),
+                         "traffic_unit": "DRAM bytes per launch (ncu, scaled to this lattice)",
+                         "bytes_per_update": bpu, "launch_ms": 1e3 * t_launch,
+                         "kernel": "k_fused2" if kernels_per_step == 1 else "two_pass (step)"},
             "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": args.steps * kernels_per_step,
             "clocks": clocks, "variants": variants, "adjoint": adjoint,
             "mass": d[0],

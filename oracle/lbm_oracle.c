@@ -412,6 +412,14 @@ void or_set_state(or_sim *s, const double *A) { memcpy(s->A, A, sizeof(double) *
 void or_get_state(const or_sim *s, double *A) { memcpy(A, s->A, sizeof(double) * NQ * s->n); }
 int64_t or_step_count(const or_sim *s) { return s->step; }
 
+/* Threads the parallel row loops use (1 without OpenMP); the results do not depend on it. */
+#ifdef _OPENMP
+#include <omp.h>
+int or_threads(void) { return omp_get_max_threads(); }
+#else
+int or_threads(void) { return 1; }
+#endif
+
 /* --------------------------------------------------------------- a step --- */
 
 /* stages 1-3 for every node: pulled populations, rho, j, psi (walls: psi(rho_s)).

@@ -52,6 +52,8 @@ def _load():
         lib.or_step.argtypes = [ctypes.c_void_p, ctypes.c_int64]
         lib.or_step_count.restype = ctypes.c_int64
         lib.or_step_count.argtypes = [ctypes.c_void_p]
+        lib.or_threads.restype = ctypes.c_int
+        lib.or_threads.argtypes = []
         lib.or_fields.argtypes = [ctypes.c_void_p] + [dp] * 8
         lib.or_diagnostics.argtypes = [ctypes.c_void_p, dp]
         lib.or_p_eos.restype = d
@@ -118,6 +120,11 @@ class Params:
             v = getattr(self, f.name)
             setattr(c, f.name, int(v) if isinstance(v, bool) else v)
         return c
+
+
+def threads() -> int:
+    """Threads of the oracle's parallel row loops (OMP_NUM_THREADS at first use)."""
+    return int(_load().or_threads())
 
 
 def p_eos(params: Params, rho: float) -> float:
