@@ -29,11 +29,12 @@ RHO_G, RHO_L = 0.009291723294794338, 0.3581443962580134  # Maxwell densities of 
 T_07 = 0.7 * 0.3773 / 4.0
 TAU = 1.0
 BYTES = {"f64": 144, "f32": 72, "f16dev": 36, "bf16dev": 36}
-# DRAM bytes per lattice update of the packed fused kernel (k_fused2), scaled from one ncu capture
-# (dram__bytes_read.sum + dram__bytes_write.sum of one launch at 4096 x 4096; profiles/k_fused2_*).
+# DRAM bytes per lattice update of the packed fused kernel (k_fused2), from one ncu capture
+# (dram__bytes_read.sum + dram__bytes_write.sum of one launch at 4096 x 4096; profiles/k_fused2_*;
+# f16dev: the per-node reference mode), scaled to a launch by the updates it makes.
 # Valid for the kernel as captured; an entry is removed when the kernel changes until it is captured
 # again (the line then reports traffic null).
-TRAFFIC_PER_UPDATE = {}
+TRAFFIC_PER_UPDATE = {"f32": 73.9, "f16dev": 44.1}
 HBM_FALLBACK = 6800.0
 
 
@@ -465,7 +466,8 @@ def main():
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                          "frac": achieved / hbm, "peak_kind": peak_kind,
                          "traffic": (TRAFFIC_PER_UPDATE[args.precision] * n * n
-                                     if kernels_per_step == 1 and TRAFFIC_PER_UPDATE.get(args.precision) else None),
+                                     if kernels_per_step == 1 and TRAFFIC_PER_UPDATE.get(args.precision)
+                                     and (args.precision == "f32" or args.node_ref) else None),
                          "traffic_unit": "DRAM bytes per launch (ncu, scaled to this lattice)",
                          "bytes_per_update": bpu, "launch_ms": 1e3 * t_launch,
                          "kernel": "k_fused2" if kernels_per_step == 1 else "two_pass (step)"},
