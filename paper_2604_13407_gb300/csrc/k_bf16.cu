@@ -42,6 +42,7 @@ Launchers launchers_bf16()
     L.get_state = &TwoPass<__nv_bfloat16>::get_state;
     L.set_state = &TwoPass<__nv_bfloat16>::set_state;
     L.fused_align = FusedGeom<__nv_bfloat16>::HX;
+    L.fused_geometry = LBM_FUSED_PAIRS;
     return L;
 }
 

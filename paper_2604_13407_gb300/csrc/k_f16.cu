@@ -42,6 +42,7 @@ Launchers launchers_f16()
     L.get_state = &TwoPass<__half>::get_state;
     L.set_state = &TwoPass<__half>::set_state;
     L.fused_align = FusedGeom<__half>::HX;
+    L.fused_geometry = LBM_FUSED_PAIRS;
     return L;
 }
 

@@ -49,6 +49,7 @@ Launchers launchers_f32()
     L.adj_blocks = &Adjoint<float>::blocks;
     L.adj_reduce = &Adjoint<float>::reduce;
     L.fused_align = FusedGeom<float>::HX;
+    L.fused_geometry = LBM_FUSED_PAIRS;
     return L;
 }
 

@@ -90,6 +90,18 @@ template <> struct Pair2<__nv_bfloat16> {
 };
 #undef LBM_DEC_PAIR
 
+// One already-scaled FP32 value rounded to the storage type (as the pair stores round).
+template <class S> struct Codec2;
+template <> struct Codec2<float> {
+    static __device__ __forceinline__ void put(float *p, float v) { *p = v; }
+};
+template <> struct Codec2<__half> {
+    static __device__ __forceinline__ void put(__half *p, float v) { *p = __float2half_rn(v); }
+};
+template <> struct Codec2<__nv_bfloat16> {
+    static __device__ __forceinline__ void put(__nv_bfloat16 *p, float v) { *p = __float2bfloat16_rn(v); }
+};
+
 __device__ __forceinline__ v2 load_ref_pair(const float *p, int off)
 {
     if (off == 0) return v2{*reinterpret_cast<const float2 *>(p)};
@@ -131,10 +143,81 @@ __device__ __forceinline__ void external_force_pair(const KParams &kp, int64_t n
         }                                                                                                     \
     }
 
+// ----------------------------------------------------- general geometry ------
+// Solid flags of columns c0 - 1 .. c0 + 2 of lattice row y (bit k = column c0 - 1 + k), with
+// periodic wrapping; nodes beyond a non-periodic edge read as fluid (those links are walls
+// by the edge test).
+__device__ __forceinline__ int solid_window(const KParams &kp, int y, int c0)
+{
+    if (y < 0 || y >= kp.ny) {
+        if (!kp.periodic_y) return 0;
+        y = y < 0 ? y + kp.ny : y - kp.ny;
+    }
+    const uint8_t *r = kp.solid + (int64_t)y * kp.nx;
+    int bits = 0;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        int x = c0 - 1 + k;
+        if (x < 0 || x >= kp.nx) {
+            if (!kp.periodic_x) continue;
+            x = x < 0 ? x + kp.nx : x - kp.nx;
+        }
+        bits |= (r[x] != 0) << k;
+    }
+    return bits;
+}
+
+// Population k of a node near (xw, yw) read from the staged rows (for `bounce`, which asks
+// for the node itself and its neighbour along e_i by lattice coordinates), decoded to FP32
+// like the pull: `row`/`ref` point at the staged column of the pair's first node, `e` is
+// the element of the pair.
+template <class S, int W>
+struct StagedAt {
+    const KParams &kp;
+    const S *const *row;
+    const float *const *ref;
+    int e, xw, yw;
+    __device__ __forceinline__ float operator()(int k, int xx, int yy) const
+    {
+        int dx = xx - xw, dy = yy - yw;
+        if (dx > 1) dx -= kp.nx;
+        else if (dx < -1) dx += kp.nx;
+        if (dy > 1) dy -= kp.ny;
+        else if (dy < -1) dy += kp.ny;
+        const int d = 1 + dy, col = e + dx;
+        float v = Pair2<S>::load1(row[d] + k * W + col);
+        if constexpr (IsDev<S>::value) {
+            const float rf = ref[0] ? ref[d][col] : kp.cf.rho_ref;
+            v = __fmaf_rn(v, kp.cf.inv_scale, __fmul_rn(w_<float>(k), rf));
+        }
+        return v;
+    }
+};
+
+// Wall links of the pair (edges beyond a non-periodic side and solid nodes): the bounce-back
+// of the two-pass step (half-way, moving wall, interpolated), element by element.
+#define LBM_GEOM_LINK(I)                                                                                      \
+    {                                                                                                         \
+        const int ys_ = rp - ey_(I);                                                                          \
+        const bool yw_ = !kp.periodic_y && (ys_ < 0 || ys_ >= ny);                                            \
+        const int wsrc_ = I == 0 ? 0 : (ey_(I) > 0 ? win_m : (ey_(I) < 0 ? win_p : win_0));                   \
+        _Pragma("unroll") for (int e = 0; e < 2; ++e) {                                                       \
+            if ((own >> e) & 1) continue;                                                                     \
+            const int xs_ = c0 + e - ex_(I);                                                                  \
+            const bool wall_ = yw_ || (!kp.periodic_x && (xs_ < 0 || xs_ >= nx)) || ((wsrc_ >> (e - ex_(I) + 1)) & 1); \
+            if (wall_) {                                                                                      \
+                const StagedAt<S, W> at_{kp, row, ref, e, xw + e, yw};                                        \
+                const float v_ = bounce<float, I>(kp, xw + e, yw, at_, (float *)nullptr);                    \
+                if (e == 0) f_new[I].v.x = v_;                                                                \
+                else f_new[I].v.y = v_;                                                                       \
+            }                                                                                                 \
+        }                                                                                                     \
+    }
+
 #ifndef LBM_FUSED2_MINB
 #define LBM_FUSED2_MINB 2  // CTAs per SM the register allocation must allow
 #endif
-template <class S, int NW, int RING, bool PERIODIC, class O>
+template <class S, int NW, int RING, bool PERIODIC, class O, bool GEOM = false>
 __global__ void __launch_bounds__(32 * (NW + 1), LBM_FUSED2_MINB) k_fused2(KParams kp, int seg_rows)
 {
     typedef FusedLayout2<S, NW, RING> L;
@@ -237,11 +320,26 @@ __global__ void __launch_bounds__(32 * (NW + 1), LBM_FUSED2_MINB) k_fused2(KPara
         const bool got = mbar_wait_bounded(full + ((r - first) & (RING - 1)), (uint32_t)(((r - first) / RING) & 1));
         return __all_sync(0xffffffffu, got);
     };
+    // solid flags of rows rp - 1, rp, rp + 1 around the pair (general geometry only)
+    int win_m = 0, win_0 = 0, win_p = 0, own_old = 0;
+    if constexpr (GEOM) {
+        if (kp.solid) {
+            win_0 = solid_window(kp, yb - 2, c0);
+            win_p = solid_window(kp, yb - 1, c0);
+        }
+    }
     bool ok = wait_full(first) && wait_full(first + 1);
     for (int rp = yb - 1; rp <= ye && ok; ++rp) {
         if (!wait_full(rp + 1)) {
             ok = false;
             break;
+        }
+        int own = 0;  // solid flags of the pair in row rp
+        if constexpr (GEOM) {
+            win_m = win_0;
+            win_0 = win_p;
+            win_p = kp.solid ? solid_window(kp, rp + 1, c0) : 0;
+            own = (win_0 >> 1) & 3;
         }
         const bool row_out = !PERIODIC && !kp.periodic_y && (rp < 0 || rp >= ny);
         v2 f_new[9], rho_new = S2(0.f), psi_new = psi_s;
@@ -260,7 +358,7 @@ __global__ void __launch_bounds__(32 * (NW + 1), LBM_FUSED2_MINB) k_fused2(KPara
             // of row rp - e_iy
             LBM_PULL_PAIR(0) LBM_PULL_PAIR(1) LBM_PULL_PAIR(2) LBM_PULL_PAIR(3) LBM_PULL_PAIR(4)
             LBM_PULL_PAIR(5) LBM_PULL_PAIR(6) LBM_PULL_PAIR(7) LBM_PULL_PAIR(8)
-            if (!PERIODIC) {
+            if (!PERIODIC && !GEOM) {
                 // links whose source lies beyond a non-periodic edge: half-way bounce-back
 #pragma unroll
                 for (int i = 1; i < 9; ++i) {
@@ -284,6 +382,14 @@ __global__ void __launch_bounds__(32 * (NW + 1), LBM_FUSED2_MINB) k_fused2(KPara
                     }
                 }
             }
+            if constexpr (GEOM) {
+                if (kp.solid || kp.q || kp.wall_u) {
+                    const int yw = rp < 0 ? rp + ny : (rp >= ny ? rp - ny : rp);
+                    const int xw = c0 < 0 ? c0 + nx : (c0 >= nx ? c0 - nx : c0);
+                    LBM_GEOM_LINK(1) LBM_GEOM_LINK(2) LBM_GEOM_LINK(3) LBM_GEOM_LINK(4)
+                    LBM_GEOM_LINK(5) LBM_GEOM_LINK(6) LBM_GEOM_LINK(7) LBM_GEOM_LINK(8)
+                }
+            }
             // the pulled populations are kept in rest-state deviation form for the collision
             {
                 v2 f[9];
@@ -293,6 +399,21 @@ __global__ void __launch_bounds__(32 * (NW + 1), LBM_FUSED2_MINB) k_fused2(KPara
             }
             rho_new = density_dev(f_new);
             psi_new = psi_v<v2>(kp, rho_new);
+            if constexpr (GEOM) {
+                if (own) {
+                    // solid nodes: psi of the virtual wall density; rho 1 keeps the unused
+                    // arithmetic of the pair finite
+                    const int yw = rp < 0 ? rp + ny : (rp >= ny ? rp - ny : rp);
+#pragma unroll
+                    for (int e = 0; e < 2; ++e) {
+                        if (!((own >> e) & 1)) continue;
+                        const int xe = c0 + e < 0 ? c0 + e + nx : (c0 + e >= nx ? c0 + e - nx : c0 + e);
+                        const float ps = kp.wall_psi ? float(kp.wall_psi[(int64_t)yw * nx + xe]) : kp.cf.psi_s;
+                        if (e == 0) psi_new.v.x = ps, rho_new.v.x = 1.f;
+                        else psi_new.v.y = ps, rho_new.v.y = 1.f;
+                    }
+                }
+            }
         }
         __syncwarp();
         // row rp - 1 is not needed any more by this warp
@@ -302,7 +423,7 @@ __global__ void __launch_bounds__(32 * (NW + 1), LBM_FUSED2_MINB) k_fused2(KPara
         const float a0 = __shfl_up_sync(0xffffffffu, psi_m1.v.y, 1), b0 = __shfl_down_sync(0xffffffffu, psi_m1.v.x, 1);
         const float ap = __shfl_up_sync(0xffffffffu, psi_new.v.y, 1), bp = __shfl_down_sync(0xffffffffu, psi_new.v.x, 1);
         const int y = rp - 1;
-        if (y >= yb && collides) {
+        if (y >= yb && collides && (!GEOM || own_old != 3)) {
             {
                 v2 fb[9];
                 // rows y-1 (m), y (0), y+1 (p); left (L), centre, right (R) columns of each node
@@ -316,7 +437,23 @@ __global__ void __launch_bounds__(32 * (NW + 1), LBM_FUSED2_MINB) k_fused2(KPara
                 external_force_pair<O>(kp, (int64_t)y * nx + c0, rho_old, Fex, Fey);
                 collide_v<v2, O>(kp, f_old, rho_old, psi_m1, Sx, Sy, Fex, Fey, fb, ux, uy);
                 S *out = static_cast<S *>(kp.dst) + (int64_t)y * kp.pitch + c0;
-                if (!dev) {
+                if (GEOM && own_old) {
+                    // one node of the pair is solid: store the fluid one alone
+                    const int e = own_old == 1 ? 1 : 0;
+                    const float rr = e ? rho_old.v.y : rho_old.v.x;
+                    if (has_ref) kp.ref_dst[(int64_t)y * kp.pitch + c0 + e] = rr;
+#pragma unroll
+                    for (int i = 0; i < 9; ++i) {
+                        const float fv = e ? fb[i].v.y : fb[i].v.x;
+                        if constexpr (IsDev<S>::value) {
+                            const int wc = i == 0 ? 0 : (i <= 4 ? 1 : 5);
+                            const float nw = has_ref ? -kp.cf.scale * __fmul_rn(kp.c2.w[wc].x, rr) : kp.c2.enc[wc].x;
+                            Codec2<S>::put(out + i * kp.plane + e, __fmaf_rn(fv, kp.cf.scale, nw));
+                        } else {
+                            out[i * kp.plane + e] = fv;
+                        }
+                    }
+                } else if (!dev) {
 #pragma unroll
                     for (int i = 0; i < 9; ++i) Pair2<S>::store(out + i * kp.plane, fb[i]);
                 } else if (has_ref) {
@@ -337,6 +474,7 @@ __global__ void __launch_bounds__(32 * (NW + 1), LBM_FUSED2_MINB) k_fused2(KPara
         psi_m2 = psi_m1;
         psi_m1 = psi_new;
         rho_old = rho_new;
+        own_old = own;
 #pragma unroll
         for (int i = 0; i < 9; ++i) f_old[i] = f_new[i];
     }
@@ -349,10 +487,10 @@ __global__ void __launch_bounds__(32 * (NW + 1), LBM_FUSED2_MINB) k_fused2(KPara
 template <class S, int NW, int RING>
 struct Fused2 {
     typedef FusedLayout2<S, NW, RING> L;
-    template <bool P, class O>
+    template <bool P, class O, bool GEOM = false>
     static cudaError_t launch_one(const KParams &kp, cudaStream_t st)
     {
-        cudaError_t e = ensure_smem_attribute(k_fused2<S, NW, RING, P, O>, kp.device, (int)L::bytes(true));
+        cudaError_t e = ensure_smem_attribute(k_fused2<S, NW, RING, P, O, GEOM>, kp.device, (int)L::bytes(true));
         if (e != cudaSuccess) return e;
         const int sms = kp.sm_count > 0 ? kp.sm_count : 148;
         const int strips = (kp.nx + L::TX - 1) / L::TX;
@@ -366,7 +504,7 @@ struct Fused2 {
         if (nseg < 1) nseg = 1;
         const int seg_rows = (kp.ny + nseg - 1) / nseg;
         nseg = (kp.ny + seg_rows - 1) / seg_rows;
-        return launch_dependent(k_fused2<S, NW, RING, P, O>, dim3(strips, nseg), dim3(32 * (NW + 1)),
+        return launch_dependent(k_fused2<S, NW, RING, P, O, GEOM>, dim3(strips, nseg), dim3(32 * (NW + 1)),
                                 L::bytes(kp.per_node_ref != 0), st, kp, seg_rows);
     }
     // Fully periodic lattices with a constant force and one relaxation time get
@@ -374,6 +512,8 @@ struct Fused2 {
     // time; everything else reads them at run time.
     static cudaError_t launch(const KParams &kp, cudaStream_t st)
     {
+        // solid nodes, moving walls or interpolated links: the general-geometry instantiation
+        if (kp.solid || kp.q || kp.wall_u) return launch_one<false, RuntimeOpts, true>(kp, st);
         if (kp.periodic_x && kp.periodic_y && kp.force_mode == 0 && !kp.var_tau) {
             if (IsDev<S>::value && kp.per_node_ref)
                 return kp.improved ? launch_one<true, Opts<1, 0, 0, 1>>(kp, st) : launch_one<true, Opts<0, 0, 0, 1>>(kp, st);

@@ -256,7 +256,7 @@ static bool fused_possible(const lbm_ctx *c)
 {
     if (!c->L.fused_pass) return false;
     const lbm_params &p = c->p;
-    if (c->solid || c->q || c->wall_u) return false;
+    if ((c->solid || c->q || c->wall_u) && !c->L.fused_geometry) return false;
     if (c->L.fused_align <= 0 || p.nx % c->L.fused_align != 0) return false;
     // the wrapped halo segment of the last strip must fit inside the lattice
     if (p.nx < c->L.fused_tile_x + 16 || p.ny < 4) return false;

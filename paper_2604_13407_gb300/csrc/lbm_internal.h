@@ -138,6 +138,7 @@ struct Launchers {
     // fused kernel launch constraints
     int fused_tile_x;     // strip width in nodes
     int fused_align;      // nx must be a multiple of this
+    int fused_geometry;   // 1: the fused kernel handles solid nodes, moving and interpolated walls
 };
 
 Launchers launchers_f64();

@@ -31,6 +31,60 @@ def geometries():
 GEOMS = geometries()
 
 
+def wall_geometries():
+    """Fused-kernel sizes of the solid-wall cases: the 45-degree banded channel (solid bands
+    where (x - y) mod 256 < 2, viscosity ratio 10) and the annulus with a resting inner and a
+    moving outer cylinder through interpolated (Bouzidi) links."""
+    T, rg, rl = cs_case()
+    g = {}
+    n = 256
+    f = 1e-6
+    p = cs_params(nx=n, ny=n, periodic_x=True, periodic_y=True, Fx=f / 2 ** 0.5, Fy=f / 2 ** 0.5,
+                  tau_l=1.0, tau_g=0.55, scheme=1)
+    g["oblique256"] = GC.Case("oblique256", p, I.oblique_slab(n, rl, rg, 90), 400, solid=I.oblique_band_walls(n))
+    solid, wall_u, q = I.annulus(n, n, 30.3, 118.6, u_wall_out=0.01)
+    c0 = (n - 1) / 2
+    r = np.hypot(np.arange(n)[None, :] - c0, np.arange(n)[:, None] - c0)
+    ring = rg + 0.5 * (rl - rg) * (np.tanh(2 * (r - 55.0) / 4.0) - np.tanh(2 * (r - 88.0) / 4.0))
+    p = cs_params(nx=n, ny=n, periodic_x=True, periodic_y=True, scheme=1)
+    g["annulus256"] = GC.Case("annulus256", p, np.where(solid == 1, rg, ring), 300, solid=solid, wall_u=wall_u, q=q)
+    return g
+
+
+WALL_GEOMS = wall_geometries()
+
+
+@pytest.mark.parametrize("geom", sorted(WALL_GEOMS))
+def test_fused_with_solid_walls_matches_oracle(geom):
+    """One pass per step on solid-wall geometry (half-way, moving and interpolated links):
+    the fused FP32 kernel against the FP64 oracle, every fluid node, 1e-4 of max |u| and of
+    rho; FP64 contexts keep the two-pass kernels for such geometry."""
+    c = WALL_GEOMS[geom]
+    o = GC.run_oracle(c)
+    g = GC.run_gpu(c, lbm.F32, lbm.KERNEL_AUTO)
+    assert g.kernel_in_use == lbm.KERNEL_FUSED
+    e_rho, e_u = GC.field_errors(g, o, c.solid)
+    print("fused FP32 %s: e_u %.3e e_rho %.3e" % (geom, e_u, e_rho))
+    assert e_u < 1e-4 and e_rho < 1e-4, (e_rho, e_u)
+    assert GC.run_gpu(c, lbm.F64, lbm.KERNEL_AUTO, steps=1).kernel_in_use == lbm.KERNEL_TWO_PASS
+
+
+@pytest.mark.parametrize("prec,kw", [(lbm.F32, {}), (lbm.F16DEV, {"per_node_ref": 1}), (lbm.BF16DEV, {"per_node_ref": 1})])
+@pytest.mark.parametrize("geom", sorted(WALL_GEOMS))
+def test_fused_with_solid_walls_equals_two_pass(geom, prec, kw):
+    """The general-geometry fused kernel against the two-pass kernel on the fluid nodes
+    (solid nodes hold no state), to the rounding of the packed arithmetic."""
+    c = WALL_GEOMS[geom]
+    a = GC.run_gpu(c, prec, lbm.KERNEL_TWO_PASS, steps=100, **kw)
+    b = GC.run_gpu(c, prec, lbm.KERNEL_FUSED, steps=100, **kw)
+    assert b.kernel_in_use == lbm.KERNEL_FUSED
+    fluid = c.solid == 0
+    A, B = a.get_state()[:, fluid], b.get_state()[:, fluid]
+    tol = 1e-5 if prec == lbm.F32 else 2e-3
+    assert np.all(np.isfinite(B))
+    assert np.abs(A - B).max() < tol * np.abs(A).max(), np.abs(A - B).max() / np.abs(A).max()
+
+
 @pytest.mark.parametrize("prec,kw", PRECS)
 @pytest.mark.parametrize("geom", sorted(GEOMS))
 def test_fused_equals_two_pass(geom, prec, kw):
