@@ -252,6 +252,28 @@ LBM_API int64_t lbm_step_count(const lbm_ctx *ctx);
 /* Kernel actually used by lbm_step (LBM_KERNEL_TWO_PASS or LBM_KERNEL_FUSED). */
 LBM_API int32_t lbm_kernel_in_use(const lbm_ctx *ctx);
 
+/* "LB-ana" (Sec. 3.1, Figs. 3-4): the steady velocity profile of two-phase Poiseuille flow that
+ * the step itself predicts for a given density profile across the channel, from the
+ * finite-difference velocity equation of the step, Eq. (fde.ali) (channel aligned with the
+ * lattice, node spacing dx) or Eq. (fde.obl) (oblique != 0: the 45-degree channel, profile along
+ * alpha = x - y with node spacing dx/sqrt 2), with the source term of p->scheme: Q_m,6 of
+ * Eq. (qm6.ali) (aligned) or Q_m,4+6 of Eq. (obl.11) with K = (24 eps - 15)/32 (45 degrees) for
+ * the improved scheme, none for the original.  The channel's walls are half-way no-slip walls
+ * just beyond both ends of the profile.
+ *   rho[n]    density of the n fluid nodes across the channel (n >= 3), host memory
+ *   f_int[n]  the pairwise force along the profile (aligned: its component across the channel;
+ *             45 degrees: its x component), or NULL to compute it from rho by Eq. (obl.10) with
+ *             psi of p's EOS and psi(p->rho_s) at the walls (one wall node beyond each end,
+ *             two for the 45-degree bands)
+ *   F_drive   driving force density along the channel
+ *   u[n]      receives the velocity along the channel
+ * Uses p's EOS, G, k1, k2, scheme, rho_s and tau (tau_l == tau_g; nu = (tau - 1/2)/3).  Runs on
+ * the host and needs no device.  LBM_EINVAL (message in lbm_last_error(NULL)): null pointers,
+ * n < 3, tau_l != tau_g, G >= 0, a density where psi is not real and positive, a singular
+ * system. */
+LBM_API lbm_status lbm_lb_ana(const lbm_params *p, int32_t oblique, int32_t n, const double *rho,
+                              const double *f_int, double F_drive, double *u);
+
 /* Largest lattice (nx * ny) accepted by lbm_step_noalloc_f32. */
 #define LBM_NOALLOC_MAX_NODES (1 << 20)
 

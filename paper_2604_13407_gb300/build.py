@@ -29,6 +29,7 @@ UNITS = {
     "k_f16.cu": FAST32,
     "k_bf16.cu": FAST32,
     "lbm_noalloc.cu": FAST32,
+    "lbm_lbana.cu": [],
 }
 
 

@@ -779,6 +779,9 @@ cudaError_t ensure_smem_attribute_ptr(const void *kernel, int device, int bytes)
     return e;
 }
 
+// psi of the EOS of *p at rho (the host evaluation create uses), for lbm_lbana.cu.
+double eos_psi(const lbm_params &p, double rho) { return host_psi(p, rho); }
+
 // Record a message for lbm_last_error(NULL).
 lbm_status set_global_error(lbm_status s, const std::string &msg) { return fail(nullptr, s, msg); }
 }  // namespace lbm

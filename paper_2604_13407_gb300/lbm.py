@@ -84,6 +84,7 @@ def load_library(path=None):
         "lbm_kernel_in_use": (ctypes.c_int32, [_vp]),
         "lbm_last_error": (ctypes.c_char_p, [_vp]),
         "lbm_step_noalloc_f32": (st, [_P(LbmParams), _vp, _vp, ctypes.c_int64, _vp]),
+        "lbm_lb_ana": (st, [_P(LbmParams), ctypes.c_int32, ctypes.c_int32, _dp, _dp, ctypes.c_double, _dp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -103,6 +104,26 @@ def default_params(**overrides):
             raise KeyError(k)
         setattr(p, k, int(v) if isinstance(v, bool) else v)
     return p
+
+
+def lb_ana(params, rho, F_drive, oblique=False, f_int=None):
+    """lbm_lb_ana: the steady velocity profile the step predicts for the density profile
+    rho across a two-phase channel (Eq. (fde.ali), or Eq. (fde.obl) with oblique=True).
+    Host arrays; no device is used."""
+    lib = load_library()
+    rho = np.ascontiguousarray(rho, dtype=np.float64)
+    u = np.empty_like(rho)
+    fp = None
+    if f_int is not None:
+        f_int = np.ascontiguousarray(f_int, dtype=np.float64)
+        if f_int.shape != rho.shape:
+            raise ValueError("f_int must have the shape of rho")
+        fp = f_int.ctypes.data_as(_dp)
+    st = lib.lbm_lb_ana(ctypes.byref(params), int(bool(oblique)), len(rho), rho.ctypes.data_as(_dp), fp,
+                        float(F_drive), u.ctypes.data_as(_dp))
+    if st != 0:
+        raise LbmError(st, lib.lbm_last_error(None).decode())
+    return u
 
 
 def _is_torch_cuda(a):
