@@ -7,8 +7,10 @@ rho = (rho_l + rho_g)/2 (1 + U(-0.01, 0.01)) with SplitMix64 seed 5, u = 0.  One
 one lattice update of every node.  Inputs (two 2.4 GB population buffers in FP32) are
 far larger than the 129 MB L2, so no flush is needed between steps.
 
-Prints one JSON line.  --impl reference times the FP64 CPU oracle instead (bounded
-sample of the same workload on the host cores).
+Prints one JSON line.  With --variants (the default) it also times the other storage types
+and the original scheme on this workload, and the one-pass step on lattices shaped like the
+two-phase channel, annulus and falling-droplet configurations ("geometry").  --impl reference
+times the FP64 CPU oracle instead (bounded sample of the same workload on the host cores).
 """
 import argparse
 import json
@@ -34,7 +36,7 @@ BYTES = {"f64": 144, "f32": 72, "f16dev": 36, "bf16dev": 36}
 # f16dev: the per-node reference mode), scaled to a launch by the updates it makes.
 # Valid for the kernel as captured; an entry is removed when the kernel changes until it is captured
 # again (the line then reports traffic null).
-TRAFFIC_PER_UPDATE = {"f32": 73.9, "f16dev": 44.1}
+TRAFFIC_PER_UPDATE = {}  # the kernels changed after the last capture
 HBM_FALLBACK = 6800.0
 
 
@@ -232,6 +234,72 @@ def adjoint_cost(precision, nsteps, checkpoint_every=200, nx=256, ny=1024, radiu
             "ratio": out["adjoint"] / out["forward"], "backward_ms_per_step": back,
             "backward_ratio": back / out["forward"], "steps": nsteps, "checkpoint_every": checkpoint_every,
             "lattice": "%dx%d" % (nx, ny)}
+
+
+def geometry_cases():
+    """Synthetic lattices shaped like the named two-phase configurations, same EOS as the
+    headline workload (Carnahan-Starling at 0.7 T_c, eps 1.895), improved scheme:
+      oblique_channel_512: 512 x 512 periodic, 45-degree channel between two-node solid bands
+        where (x - y) mod 512 < 2, liquid slab across half the width, tau_l = 1.0, tau_g = 0.55,
+        force 4e-9 along the bands;
+      annulus_1024: 1024 x 1024, solid where r < 128 (at rest) or r > 480 (moving tangentially
+        at 0.01), interpolated links, liquid annulus 200 < r < 320, tau 0.8;
+      falling_droplet_512x4096: walls at x = -1/2 and 511.5, periodic y, radius-40 droplet at a
+        seed-4 jittered centre near (256, 3500), buoyant gravity (rho - rho_g) g, |g| = 2e-6, tau 0.8.
+    Yields (name, params overrides, rho, solid, wall_u, q)."""
+    from paper_2604_13407_gb300 import inputs as I
+    n = 512
+    solid = I.oblique_band_walls(n)
+    rho = np.where(solid == 1, RHO_G, I.oblique_slab(n, RHO_L, RHO_G, n // 2))
+    f = 4e-9 / math.sqrt(2.0)
+    yield ("oblique_channel_512", dict(nx=n, ny=n, periodic_x=1, periodic_y=1, Fx=f, Fy=f, tau_l=1.0, tau_g=0.55),
+           rho, solid, None, None)
+    n = 1024
+    solid, wall_u, q = I.annulus(n, n, 128.0, 480.0, u_wall_out=0.01)
+    c0 = (n - 1) / 2.0
+    r = np.hypot(np.arange(n)[None, :] - c0, np.arange(n)[:, None] - c0)
+    ring = RHO_G + 0.5 * (RHO_L - RHO_G) * (np.tanh(2 * (r - 200.0) / 4.0) - np.tanh(2 * (r - 320.0) / 4.0))
+    yield ("annulus_1024", dict(nx=n, ny=n, periodic_x=1, periodic_y=1, tau_l=0.8, tau_g=0.8),
+           np.where(solid == 1, RHO_G, ring), solid, wall_u, q)
+    nx, ny = 512, 4096
+    cx, cy = I.jittered_centre(4, 256.0, 3500.0)
+    yield ("falling_droplet_512x4096", dict(nx=nx, ny=ny, periodic_x=0, periodic_y=1, force_mode=1, Fy=-2e-6,
+                                            tau_l=0.8, tau_g=0.8),
+           I.droplet(nx, ny, RHO_L, RHO_G, 40.0, cx, cy, periodic_x=False, periodic_y=True), None, None, None)
+
+
+def geometry_throughput(hbm, steps=2000, warmup=20):
+    """GLUPS of the one-pass step on the geometry_cases lattices (CUDA events on the
+    launching stream).  Bytes per update: the population read and write of the storage
+    type, plus the node's solid flag where there is a mask; interpolated-link distances and
+    wall velocities are read only at wall links.  The two smaller lattices' state fits in
+    L2 (and the step is bound by latency, not by HBM), so their fraction of the HBM copy
+    bandwidth is reported for comparison only."""
+    import torch
+    from paper_2604_13407_gb300 import lbm
+    out = {}
+    for name, over, rho, solid, wall_u, q in geometry_cases():
+        for prec in ("f32", "f16dev"):
+            pid = lbm.F32 if prec == "f32" else lbm.F16DEV
+            p = lbm.default_params(precision=pid, scheme=1, T=T_07, rho_l=RHO_L, rho_g=RHO_G, rho_s=RHO_G,
+                                   rho_ref=0.5 * (RHO_L + RHO_G), per_node_ref=1,
+                                   storage_scale_log2=18 if prec == "f16dev" else 0, **over)
+            s = lbm.Simulation(p, stream=torch.cuda.current_stream())
+            if solid is not None:
+                s.set_geometry(solid, wall_u, q, None)
+            s.init_fields(rho)
+            nodes = over["nx"] * over["ny"]
+            t = timed_steps(s, steps, warmup, False)
+            g = nodes * steps / t / 1e9
+            b = BYTES[prec] + (8 if prec == "f16dev" else 0) + (1 if solid is not None else 0)
+            # two population buffers (and two reference planes for per-node FP16)
+            state_mb = (BYTES[prec] + (8 if prec == "f16dev" else 0)) * nodes / 1e6
+            out["%s_%s" % (name, prec)] = {
+                "GLUPS": g, "us_per_step": 1e6 * t / steps, "bytes_per_update": b, "achieved_GBs": b * g,
+                "frac_of_hbm": b * g / hbm, "state_MB": state_mb, "steps": steps,
+                "kernel": "fused" if s.kernel_in_use == lbm.KERNEL_FUSED else "two_pass"}
+            s.close()
+    return out
 
 
 # ------------------------------------------------------------ CPU legs ----
@@ -436,6 +504,10 @@ def main():
                 variants[name]["bound"] = "fp64 alu"
             s2.close()
 
+    geometry = None
+    if args.variants and rank == 0 and not dist_on:
+        geometry = geometry_throughput(hbm)
+
     adjoint = None
     if args.adjoint and rank == 0 and not dist_on:
         adjoint = {"workload": "droplet in a 256x1024 channel (radius 20, buoyant g 2e-6, walls in x, periodic y), "
@@ -472,7 +544,7 @@ def main():
                          "bytes_per_update": bpu, "launch_ms": 1e3 * t_launch,
                          "kernel": "k_fused2" if kernels_per_step == 1 else "two_pass (step)"},
             "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": args.steps * kernels_per_step,
-            "clocks": clocks, "variants": variants, "adjoint": adjoint,
+            "clocks": clocks, "variants": variants, "geometry": geometry, "adjoint": adjoint,
             "mass": d[0],
         }
         print(json.dumps(line))

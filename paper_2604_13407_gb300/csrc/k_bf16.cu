@@ -19,7 +19,7 @@
 #define LBM_FUSED2_NW 4
 #endif
 #ifndef LBM_FUSED2_RING
-#define LBM_FUSED2_RING 4
+#define LBM_FUSED2_RING 8  // 16-bit rows are half as large: 8 staged rows fit 4 CTAs per SM
 #endif
 
 namespace lbm {

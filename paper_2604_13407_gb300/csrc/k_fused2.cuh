@@ -147,14 +147,19 @@ __device__ __forceinline__ void external_force_pair(const KParams &kp, int64_t n
 // Solid flags of columns c0 - 1 .. c0 + 2 of lattice row y (bit k = column c0 - 1 + k), with
 // periodic wrapping; nodes beyond a non-periodic edge read as fluid (those links are walls
 // by the edge test).
-__device__ __forceinline__ int solid_window(const KParams &kp, int y, int c0)
+// The four flags are fetched one row ahead of their use (solid_fetch) and combined when
+// the row is reached (solid_bits), so the latency of the global loads overlaps a row of work.
+struct SolidRow {
+    int v[4];
+};
+__device__ __forceinline__ SolidRow solid_fetch(const KParams &kp, int y, int c0)
 {
+    SolidRow w{{0, 0, 0, 0}};
     if (y < 0 || y >= kp.ny) {
-        if (!kp.periodic_y) return 0;
+        if (!kp.periodic_y) return w;
         y = y < 0 ? y + kp.ny : y - kp.ny;
     }
     const uint8_t *r = kp.solid + (int64_t)y * kp.nx;
-    int bits = 0;
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
         int x = c0 - 1 + k;
@@ -162,20 +167,27 @@ __device__ __forceinline__ int solid_window(const KParams &kp, int y, int c0)
             if (!kp.periodic_x) continue;
             x = x < 0 ? x + kp.nx : x - kp.nx;
         }
-        bits |= (r[x] != 0) << k;
+        w.v[k] = r[x];
     }
-    return bits;
+    return w;
+}
+__device__ __forceinline__ int solid_bits(const SolidRow &w)
+{
+    return (w.v[0] != 0) | (w.v[1] != 0) << 1 | (w.v[2] != 0) << 2 | (w.v[3] != 0) << 3;
 }
 
 // Population k of a node near (xw, yw) read from the staged rows (for `bounce`, which asks
 // for the node itself and its neighbour along e_i by lattice coordinates), decoded to FP32
 // like the pull: `row`/`ref` point at the staged column of the pair's first node, `e` is
 // the element of the pair.
+// The three row pointers are separate members and chosen by comparison: an array indexed
+// by a run-time row would be placed in local memory, and with it every staged-row access of
+// the kernel.
 template <class S, int W>
 struct StagedAt {
     const KParams &kp;
-    const S *const *row;
-    const float *const *ref;
+    const S *rm, *r0, *rp;
+    const float *fm, *f0, *fp;
     int e, xw, yw;
     __device__ __forceinline__ float operator()(int k, int xx, int yy) const
     {
@@ -184,10 +196,12 @@ struct StagedAt {
         else if (dx < -1) dx += kp.nx;
         if (dy > 1) dy -= kp.ny;
         else if (dy < -1) dy += kp.ny;
-        const int d = 1 + dy, col = e + dx;
-        float v = Pair2<S>::load1(row[d] + k * W + col);
+        const int col = e + dx;
+        const S *r = dy < 0 ? rm : (dy > 0 ? rp : r0);
+        float v = Pair2<S>::load1(r + k * W + col);
         if constexpr (IsDev<S>::value) {
-            const float rf = ref[0] ? ref[d][col] : kp.cf.rho_ref;
+            const float *f = dy < 0 ? fm : (dy > 0 ? fp : f0);
+            const float rf = f0 ? f[col] : kp.cf.rho_ref;
             v = __fmaf_rn(v, kp.cf.inv_scale, __fmul_rn(w_<float>(k), rf));
         }
         return v;
@@ -206,7 +220,7 @@ struct StagedAt {
             const int xs_ = c0 + e - ex_(I);                                                                  \
             const bool wall_ = yw_ || (!kp.periodic_x && (xs_ < 0 || xs_ >= nx)) || ((wsrc_ >> (e - ex_(I) + 1)) & 1); \
             if (wall_) {                                                                                      \
-                const StagedAt<S, W> at_{kp, row, ref, e, xw + e, yw};                                        \
+                const StagedAt<S, W> at_{kp, row[0], row[1], row[2], ref[0], ref[1], ref[2], e, xw + e, yw};  \
                 const float v_ = bounce<float, I>(kp, xw + e, yw, at_, (float *)nullptr);                    \
                 if (e == 0) f_new[I].v.x = v_;                                                                \
                 else f_new[I].v.y = v_;                                                                       \
@@ -236,6 +250,10 @@ __global__ void __launch_bounds__(32 * (NW + 1), LBM_FUSED2_MINB) k_fused2(KPara
     const int ye = min(yb + seg_rows, ny);
     const int first = yb - 2, last = ye + 1;  // staged rows
     const int x_lo = x0 - HX;
+    // consumer warps whose 60 columns all lie beyond the lattice (the last strip of a lattice
+    // whose width is not a multiple of the strip) leave at once and are not counted by the
+    // ring's release barriers
+    const int nw_act = min(NW, (nx - x0 + 59) / 60);
 
     // the state this step reads is the one the previous step wrote, and this step writes
     // the buffer the previous step read: nothing global is touched before it has completed
@@ -244,13 +262,14 @@ __global__ void __launch_bounds__(32 * (NW + 1), LBM_FUSED2_MINB) k_fused2(KPara
     if (threadIdx.x == 0) {
         for (int s = 0; s < RING; ++s) {
             mbar_init(full + s, 1);
-            mbar_init(empty + s, NW);
+            mbar_init(empty + s, nw_act);
         }
         fence_mbar_init();
         fence_proxy_async();
     }
     __syncthreads();
 
+    if (warp < NW && warp >= nw_act) return;
     if (warp == NW) {
         // ------------------------------------------------------ producer warp
         if (lane != 0) return;
@@ -322,10 +341,12 @@ __global__ void __launch_bounds__(32 * (NW + 1), LBM_FUSED2_MINB) k_fused2(KPara
     };
     // solid flags of rows rp - 1, rp, rp + 1 around the pair (general geometry only)
     int win_m = 0, win_0 = 0, win_p = 0, own_old = 0;
+    SolidRow win_next{{0, 0, 0, 0}};  // raw flags of row rp + 2, fetched one row early
     if constexpr (GEOM) {
         if (kp.solid) {
-            win_0 = solid_window(kp, yb - 2, c0);
-            win_p = solid_window(kp, yb - 1, c0);
+            win_0 = solid_bits(solid_fetch(kp, yb - 2, c0));
+            win_p = solid_bits(solid_fetch(kp, yb - 1, c0));
+            win_next = solid_fetch(kp, yb, c0);
         }
     }
     bool ok = wait_full(first) && wait_full(first + 1);
@@ -338,7 +359,10 @@ __global__ void __launch_bounds__(32 * (NW + 1), LBM_FUSED2_MINB) k_fused2(KPara
         if constexpr (GEOM) {
             win_m = win_0;
             win_0 = win_p;
-            win_p = kp.solid ? solid_window(kp, rp + 1, c0) : 0;
+            if (kp.solid) {
+                win_p = solid_bits(win_next);
+                win_next = solid_fetch(kp, rp + 2, c0);
+            }
             own = (win_0 >> 1) & 3;
         }
         const bool row_out = !PERIODIC && !kp.periodic_y && (rp < 0 || rp >= ny);
@@ -484,6 +508,21 @@ __global__ void __launch_bounds__(32 * (NW + 1), LBM_FUSED2_MINB) k_fused2(KPara
 }
 #undef LBM_PULL_PAIR
 
+// Grid shape: about CTAS_PER_SM CTAs per SM, each a strip of rows no shorter than ROWS_L2
+// rows when both population buffers together take at most L2_STATE_MB, else ROWS_HBM rows.
+#ifndef LBM_FUSED2_CTAS_PER_SM
+#define LBM_FUSED2_CTAS_PER_SM 16
+#endif
+#ifndef LBM_FUSED2_ROWS_L2
+#define LBM_FUSED2_ROWS_L2 4
+#endif
+#ifndef LBM_FUSED2_ROWS_HBM
+#define LBM_FUSED2_ROWS_HBM 16
+#endif
+#ifndef LBM_FUSED2_L2_STATE_MB
+#define LBM_FUSED2_L2_STATE_MB 64
+#endif
+
 template <class S, int NW, int RING>
 struct Fused2 {
     typedef FusedLayout2<S, NW, RING> L;
@@ -494,11 +533,11 @@ struct Fused2 {
         if (e != cudaSuccess) return e;
         const int sms = kp.sm_count > 0 ? kp.sm_count : 148;
         const int strips = (kp.nx + L::TX - 1) / L::TX;
-        int nseg = (16 * sms + strips - 1) / strips;
+        int nseg = (LBM_FUSED2_CTAS_PER_SM * sms + strips - 1) / strips;
         // segments re-read 3 halo rows; a lattice whose two population buffers fit in L2 reads
         // them from L2, so it may be cut into short segments (more CTAs), a larger one not
         const double state_bytes = 2.0 * 9.0 * (double)kp.plane * sizeof(S);
-        const int min_rows = state_bytes <= 64.0 * 1024 * 1024 ? 4 : 16;
+        const int min_rows = state_bytes <= LBM_FUSED2_L2_STATE_MB * 1048576.0 ? LBM_FUSED2_ROWS_L2 : LBM_FUSED2_ROWS_HBM;
         const int max_seg = kp.ny / min_rows > 0 ? kp.ny / min_rows : 1;
         if (nseg > max_seg) nseg = max_seg;
         if (nseg < 1) nseg = 1;
