@@ -119,7 +119,7 @@ class ClockSampler:
 
 # -------------------------------------------------------------- GPU legs --
 
-def make_sim(n, precision, scheme=1, kernel=0, per_node_ref=1):
+def make_sim(n, precision, scheme=1, kernel=0, per_node_ref=1, rounding=1):
     import torch
     from paper_2604_13407_gb300 import lbm
     # FP16 deviations stay below 2^-2 (largest FP16 value 65504 = 2^16 - 2^5); the 2^k
@@ -128,7 +128,7 @@ def make_sim(n, precision, scheme=1, kernel=0, per_node_ref=1):
     p = lbm.default_params(nx=n, ny=n, periodic_x=1, periodic_y=1, precision=precision, scheme=scheme,
                            kernel=kernel, per_node_ref=per_node_ref, T=T_07, rho_l=RHO_L, rho_g=RHO_G,
                            rho_s=RHO_G, rho_ref=0.5 * (RHO_L + RHO_G), storage_scale_log2=scale,
-                           tau_l=TAU, tau_g=TAU)
+                           storage_rounding=rounding, tau_l=TAU, tau_g=TAU)
     return lbm.Simulation(p, stream=torch.cuda.current_stream())
 
 
@@ -369,6 +369,8 @@ def cpu_baseline_runs():
 
 def workload_config(n, precision, node_ref=1):
     storage = precision + (" (per-node reference density)" if precision in ("f16dev", "bf16dev") and node_ref else "")
+    if precision in ("f16dev", "bf16dev"):
+        storage += ", stochastically rounded"
     return {"workload": "spinodal %dx%d periodic, Carnahan-Starling 0.7Tc, eps 1.895, improved "
                         "scheme, tau %.1f, %s population storage" % (n, n, TAU, storage),
             "nx": n, "ny": n, "storage": precision,
@@ -482,13 +484,15 @@ def main():
         for name, prec, scheme, extra in (
                 ("f32_original", "f32", 0, {}),
                 ("f16dev_node_ref", "f16dev", 1, {"per_node_ref": 1}),
+                ("f16dev_node_ref_nearest", "f16dev", 1, {"per_node_ref": 1, "storage_rounding": 0}),
                 ("bf16dev_node_ref", "bf16dev", 1, {"per_node_ref": 1}),
                 ("f16dev_global_ref", "f16dev", 1, {}),
                 ("f64", "f64", 1, {})):
-            if prec == args.precision and scheme == 1 and (prec in ("f32", "f64") or
-                                                             extra.get("per_node_ref", 0) == args.node_ref):
+            if prec == args.precision and scheme == 1 and extra.get("storage_rounding", 1) == 1 and (
+                    prec in ("f32", "f64") or extra.get("per_node_ref", 0) == args.node_ref):
                 continue
-            s2 = make_sim(n, prec_id[prec], scheme=scheme, per_node_ref=extra.get("per_node_ref", 0))
+            s2 = make_sim(n, prec_id[prec], scheme=scheme, per_node_ref=extra.get("per_node_ref", 0),
+                          rounding=extra.get("storage_rounding", 1))
             s2.init_fields(rho)
             k = max(20, args.steps // (4 if prec == "f64" else 1))
             t2 = timed_steps(s2, k, args.warmup, False)
@@ -496,6 +500,8 @@ def main():
             g = n * n * k / t2 / 1e9
             variants[name] = {"GLUPS": g, "bytes_per_update": b, "achieved_GBs": b * g, "frac": b * g / hbm,
                               "kernel": "fused" if s2.kernel_in_use == lbm.KERNEL_FUSED else "two_pass"}
+            if name == "f16dev_node_ref_nearest":
+                variants[name]["note"] = "stored deviations rounded to nearest (storage_rounding = 0)"
             if name == "f16dev_global_ref":
                 variants[name]["note"] = ("deviations from one reference density: not accurate at this density "
                                           "ratio (O(1) error); bytes and speed only")

@@ -108,6 +108,17 @@ typedef struct lbm_params {
                                        w_i rho_ref */
     int32_t storage_scale_log2;     /* FP16/BF16 storage of (f_i - w_i rho_ref) 2^k; k in
                                        [-30, 30], for FP16 in [-15, 24] */
+    int32_t storage_rounding;       /* FP16/BF16 storage, rounding of each stored deviation:
+                                       0 to nearest (ties to even); 1 (default) stochastic (rounded up
+                                       with probability equal to the discarded fraction of an
+                                       ulp, from random bits that hash the node, the
+                                       population and the step count: unbiased, and the same
+                                       in every run and in both step kernels).  Rounding to
+                                       nearest repeats the same error at every node of a
+                                       uniform region, step after step, which drifts mass and
+                                       momentum; stochastic rounding leaves a zero-mean error
+                                       (but no longer keeps mirror-symmetric states exactly
+                                       symmetric).  The initial state is rounded to nearest. */
     double a, b, R, T, K_eos;       /* EOS coefficients */
     double G;                       /* interaction strength, < 0 (Sec. 2) */
     double k1, k2;                  /* source coefficients, epsilon = -8 (k1 + k2) */

@@ -314,9 +314,11 @@ __global__ void __launch_bounds__(32 * (NW + 1)) k_fused(KParams kp, int seg_row
                 ref = rho_old;
                 kp.ref_dst[(int64_t)y * kp.pitch + col] = float(rho_old);
             }
+            const int64_t kn = (int64_t)y * kp.pitch + col;
+            const uint32_t h = IsDev<S>::value && kp.sr ? sr_hash((uint32_t)(kn >> 1), kp.sr_seed) : 0u;
 #pragma unroll
             for (int i = 0; i < 9; ++i) {
-                out[0] = Codec<S>::enc(fb[i], w_<R>(i) * ref, cst<R>(kp).scale);
+                out[0] = enc_pop<S>(kp, fb[i], w_<R>(i) * ref, cst<R>(kp).scale, kn, i, h);
                 out += kp.plane;
             }
         }

@@ -56,6 +56,7 @@ template <> struct Pair2<float> {
     }
     static __device__ __forceinline__ float load1(const float *p) { return *p; }
     static __device__ __forceinline__ void store(float *p, v2 f) { *reinterpret_cast<float2 *>(p) = f.v; }
+    static __device__ __forceinline__ void store_sr(float *p, v2 f, uint32_t) { store(p, f); }  // FP32: exact
 };
 #define LBM_DEC_PAIR(TS, T2, T)                                                                               \
     template <int OFF>                                                                                        \
@@ -79,6 +80,11 @@ template <> struct Pair2<__half> {
     LBM_DEC_PAIR(__half, __half2, "f16")
     static __device__ __forceinline__ float load1(const __half *p) { return __half2float(*p); }
     static __device__ __forceinline__ void store(__half *p, v2 f) { *reinterpret_cast<__half2 *>(p) = __float22half2_rn(f.v); }
+    // stochastic rounding with the pair's random word r (element 0 from its low half)
+    static __device__ __forceinline__ void store_sr(__half *p, v2 f, uint32_t r)
+    {
+        *reinterpret_cast<uint32_t *>(p) = SRound<__half>::pack(f.v.x, f.v.y, r);
+    }
 };
 template <> struct Pair2<__nv_bfloat16> {
     LBM_DEC_PAIR(__nv_bfloat16, __nv_bfloat162, "bf16")
@@ -86,6 +92,10 @@ template <> struct Pair2<__nv_bfloat16> {
     static __device__ __forceinline__ void store(__nv_bfloat16 *p, v2 f)
     {
         *reinterpret_cast<__nv_bfloat162 *>(p) = __float22bfloat162_rn(f.v);
+    }
+    static __device__ __forceinline__ void store_sr(__nv_bfloat16 *p, v2 f, uint32_t r)
+    {
+        *reinterpret_cast<uint32_t *>(p) = SRound<__nv_bfloat16>::pack(f.v.x, f.v.y, r);
     }
 };
 #undef LBM_DEC_PAIR
@@ -220,8 +230,18 @@ struct StagedAt {
             const int xs_ = c0 + e - ex_(I);                                                                  \
             const bool wall_ = yw_ || (!kp.periodic_x && (xs_ < 0 || xs_ >= nx)) || ((wsrc_ >> (e - ex_(I) + 1)) & 1); \
             if (wall_) {                                                                                      \
-                const StagedAt<S, W> at_{kp, row[0], row[1], row[2], ref[0], ref[1], ref[2], e, xw + e, yw};  \
-                const float v_ = bounce<float, I>(kp, xw + e, yw, at_, (float *)nullptr);                    \
+                float v_;                                                                                     \
+                if (!kp.q && !kp.wall_u) {                                                                    \
+                    /* half-way: the population that left the node toward the wall returns */                \
+                    constexpr int o_ = opp_(I);                                                               \
+                    v_ = Pair2<S>::load1(row[1] + o_ * W + e);                                                \
+                    if constexpr (IsDev<S>::value)                                                            \
+                        v_ = __fmaf_rn(v_, kp.cf.inv_scale, __fmul_rn(w_<float>(o_), ref[1] ? ref[1][e] : kp.cf.rho_ref)); \
+                    v_ = v_ + 0.f;                                                                            \
+                } else {                                                                                      \
+                    const StagedAt<S, W> at_{kp, row[0], row[1], row[2], ref[0], ref[1], ref[2], e, xw + e, yw}; \
+                    v_ = bounce<float, I>(kp, xw + e, yw, at_, (float *)nullptr);                             \
+                }                                                                                             \
                 if (e == 0) f_new[I].v.x = v_;                                                                \
                 else f_new[I].v.y = v_;                                                                       \
             }                                                                                                 \
@@ -407,7 +427,12 @@ __global__ void __launch_bounds__(32 * (NW + 1), LBM_FUSED2_MINB) k_fused2(KPara
                 }
             }
             if constexpr (GEOM) {
-                if (kp.solid || kp.q || kp.wall_u) {
+                // a link can only be a wall link when a solid node lies among columns c0 - 1 ..
+                // c0 + 2 of rows rp - 1 .. rp + 1, or those reach beyond a non-periodic edge;
+                // most pairs have neither and skip the per-link tests
+                const bool edge = (!kp.periodic_y && (rp - 1 < 0 || rp + 1 >= ny)) ||
+                                  (!kp.periodic_x && (c0 - 1 < 0 || c0 + 2 >= nx));
+                if ((kp.solid || kp.q || kp.wall_u) && (edge || (win_m | win_0 | win_p) != 0)) {
                     const int yw = rp < 0 ? rp + ny : (rp >= ny ? rp - ny : rp);
                     const int xw = c0 < 0 ? c0 + nx : (c0 >= nx ? c0 - nx : c0);
                     LBM_GEOM_LINK(1) LBM_GEOM_LINK(2) LBM_GEOM_LINK(3) LBM_GEOM_LINK(4)
@@ -461,6 +486,8 @@ __global__ void __launch_bounds__(32 * (NW + 1), LBM_FUSED2_MINB) k_fused2(KPara
                 external_force_pair<O>(kp, (int64_t)y * nx + c0, rho_old, Fex, Fey);
                 collide_v<v2, O>(kp, f_old, rho_old, psi_m1, Sx, Sy, Fex, Fey, fb, ux, uy);
                 S *out = static_cast<S *>(kp.dst) + (int64_t)y * kp.pitch + c0;
+                // random word of the pair (stochastic rounding of 16-bit storage only)
+                const uint32_t hsr = dev && kp.sr ? sr_hash((uint32_t)(((int64_t)y * kp.pitch + c0) >> 1), kp.sr_seed) : 0u;
                 if (GEOM && own_old) {
                     // one node of the pair is solid: store the fluid one alone
                     const int e = own_old == 1 ? 1 : 0;
@@ -472,7 +499,9 @@ __global__ void __launch_bounds__(32 * (NW + 1), LBM_FUSED2_MINB) k_fused2(KPara
                         if constexpr (IsDev<S>::value) {
                             const int wc = i == 0 ? 0 : (i <= 4 ? 1 : 5);
                             const float nw = has_ref ? -kp.cf.scale * __fmul_rn(kp.c2.w[wc].x, rr) : kp.c2.enc[wc].x;
-                            Codec2<S>::put(out + i * kp.plane + e, __fmaf_rn(fv, kp.cf.scale, nw));
+                            const float sv = __fmaf_rn(fv, kp.cf.scale, nw);
+                            if (kp.sr) out[i * kp.plane + e] = sr_one<S>(sv, sr_bits(hsr, i), e);
+                            else Codec2<S>::put(out + i * kp.plane + e, sv);
                         } else {
                             out[i * kp.plane + e] = fv;
                         }
@@ -486,12 +515,17 @@ __global__ void __launch_bounds__(32 * (NW + 1), LBM_FUSED2_MINB) k_fused2(KPara
                     for (int i = 0; i < 9; ++i) {
                         // (f - w_i ref) 2^k as one rounding: f 2^k - (w_i ref) 2^k
                         const v2 nwref = v2{kp.c2.m_scale} * (v2{kp.c2.w[i == 0 ? 0 : (i <= 4 ? 1 : 5)]} * rho_old);
-                        Pair2<S>::store(out + i * kp.plane, vfma(fb[i], v2{kp.c2.scale}, nwref));
+                        const v2 sv = vfma(fb[i], v2{kp.c2.scale}, nwref);
+                        if (kp.sr) Pair2<S>::store_sr(out + i * kp.plane, sv, sr_bits(hsr, i));
+                        else Pair2<S>::store(out + i * kp.plane, sv);
                     }
                 } else {
 #pragma unroll
-                    for (int i = 0; i < 9; ++i)
-                        Pair2<S>::store(out + i * kp.plane, vfma(fb[i], v2{kp.c2.scale}, v2{kp.c2.enc[i == 0 ? 0 : (i <= 4 ? 1 : 5)]}));
+                    for (int i = 0; i < 9; ++i) {
+                        const v2 sv = vfma(fb[i], v2{kp.c2.scale}, v2{kp.c2.enc[i == 0 ? 0 : (i <= 4 ? 1 : 5)]});
+                        if (kp.sr) Pair2<S>::store_sr(out + i * kp.plane, sv, sr_bits(hsr, i));
+                        else Pair2<S>::store(out + i * kp.plane, sv);
+                    }
                 }
             }
         }

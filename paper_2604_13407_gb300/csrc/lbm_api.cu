@@ -95,6 +95,7 @@ extern "C" lbm_status lbm_params_default(lbm_params *p)
     p->eos = LBM_EOS_CS;
     p->force_mode = LBM_FORCE_CONST;
     p->kernel = LBM_KERNEL_AUTO;
+    p->storage_rounding = 1;
     p->a = 1.0;
     p->b = 4.0;
     p->R = 1.0;
@@ -128,6 +129,7 @@ static lbm_status validate(lbm_ctx *c, const lbm_params &p)
     if (!(p.Lambda > 0.0)) return fail(c, LBM_EINVAL, "Lambda must be > 0");
     if (p.tau_l != p.tau_g && !(p.rho_l > p.rho_g)) return fail(c, LBM_EINVAL, "rho_l must exceed rho_g when tau_l != tau_g");
     if (p.storage_scale_log2 < -30 || p.storage_scale_log2 > 30) return fail(c, LBM_EINVAL, "storage_scale_log2 out of range");
+    if (p.storage_rounding != 0 && p.storage_rounding != 1) return fail(c, LBM_EINVAL, "storage_rounding must be 0 or 1");
     if (p.precision == LBM_F16DEV && (p.storage_scale_log2 < -15 || p.storage_scale_log2 > 24))
         return fail(c, LBM_EINVAL, "FP16 storage needs storage_scale_log2 in [-15, 24] (2^-k must be an FP16 value)");
     double rmax = p.rho_max > 0 ? p.rho_max : 1.25 * std::fmax(std::fmax(p.rho_l, p.rho_g), p.rho_s);
@@ -163,6 +165,7 @@ static void fill_constants(lbm_ctx *c)
     k.force_mode = p.force_mode;
     k.var_tau = p.tau_l != p.tau_g;
     k.per_node_ref = (p.precision >= LBM_F16DEV) && p.per_node_ref;
+    k.sr = (p.precision >= LBM_F16DEV) && p.storage_rounding;
     k.eos_a = p.a;
     k.eos_b = p.b;
     k.eos_RT = p.R * p.T;
@@ -480,10 +483,24 @@ extern "C" lbm_status lbm_init_fields(lbm_ctx *c, const double *rho, const doubl
     return LBM_OK;
 }
 
+// Seed of the stochastic-rounding bits of step t (MurmurHash3's 32-bit finaliser of the
+// step count's two halves; any well-mixed function of t would do).
+static uint32_t sr_seed_of(int64_t t)
+{
+    uint32_t h = (uint32_t)t * 0x9E3779B1u ^ (uint32_t)((uint64_t)t >> 32) * 0x85EBCA77u;
+    h ^= h >> 16;
+    h *= 0x85EBCA6Bu;
+    h ^= h >> 13;
+    h *= 0xC2B2AE35u;
+    h ^= h >> 16;
+    return h;
+}
+
 static lbm_status run_steps(lbm_ctx *c, int64_t nsteps)
 {
     for (int64_t t = 0; t < nsteps; ++t) {
         bind_buffers(c, c->cur);
+        c->kp.sr_seed = sr_seed_of(c->steps);
         if (c->fused_ok) {
             CK(c->L.fused_pass(c->kp, c->stream), "fused step kernel");
         } else {

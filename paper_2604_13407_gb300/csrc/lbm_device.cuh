@@ -103,6 +103,79 @@ template <class S> struct IsDev { static constexpr bool value = false; };
 template <> struct IsDev<__half> { static constexpr bool value = true; };
 template <> struct IsDev<__nv_bfloat16> { static constexpr bool value = true; };
 
+// ------------------------------------------------------ stochastic rounding ---
+// Optional rounding of the 16-bit storage: the scaled deviation is rounded up with a
+// probability equal to the fraction of an ulp that rounding down would discard
+// (cvt.rs.{f16x2,bf16x2}.f32: random bits are added to the discarded bits, then truncated).
+// Nodes come in pairs (2m, 2m + 1) of the padded row-major index k = y pitch + x (pitch is
+// even); the pair's random word for population i is sr_bits(sr_hash(m, seed), i), and the
+// paired conversion takes the even node's bits from the low half of the word and the odd
+// node's from the high half, so the two step kernels (one node or two per thread) round
+// every value alike.  sr_hash is MurmurHash3's 32-bit finaliser of the pair index mixed with
+// the step's seed.
+__device__ __forceinline__ uint32_t sr_hash(uint32_t pair, uint32_t seed)
+{
+    uint32_t h = pair * 0x9E3779B1u ^ seed;
+    h ^= h >> 16;
+    h *= 0x85EBCA6Bu;
+    h ^= h >> 13;
+    h *= 0xC2B2AE35u;
+    h ^= h >> 16;
+    return h;
+}
+// a different odd multiplier per population (a bijection of every low-bit window)
+__device__ __forceinline__ uint32_t sr_bits(uint32_t h, int i) { return h * (0x9E3779B9u + 0x3C6EF372u * (uint32_t)i); }
+
+template <class S> struct SRound;
+template <> struct SRound<__half> {
+    // low half <- lo, high half <- hi
+    static __device__ __forceinline__ uint32_t pack(float lo, float hi, uint32_t r)
+    {
+        uint32_t d;
+        asm("cvt.rs.f16x2.f32 %0, %1, %2, %3;" : "=r"(d) : "f"(hi), "f"(lo), "r"(r));
+        return d;
+    }
+    static __device__ __forceinline__ __half from_bits(unsigned short b)
+    {
+        __half_raw h;
+        h.x = b;
+        return __half(h);
+    }
+};
+template <> struct SRound<__nv_bfloat16> {
+    static __device__ __forceinline__ uint32_t pack(float lo, float hi, uint32_t r)
+    {
+        uint32_t d;
+        asm("cvt.rs.bf16x2.f32 %0, %1, %2, %3;" : "=r"(d) : "f"(hi), "f"(lo), "r"(r));
+        return d;
+    }
+    static __device__ __forceinline__ __nv_bfloat16 from_bits(unsigned short b)
+    {
+        __nv_bfloat16_raw h;
+        h.x = b;
+        return __nv_bfloat16(h);
+    }
+};
+// One already-scaled value rounded stochastically as element `odd` of its node pair.
+template <class S>
+__device__ __forceinline__ S sr_one(float v, uint32_t r, int odd)
+{
+    const uint32_t d = odd ? SRound<S>::pack(0.f, v, r) : SRound<S>::pack(v, 0.f, r);
+    return SRound<S>::from_bits((unsigned short)(odd ? d >> 16 : d & 0xffffu));
+}
+
+// Stored value of population i of node k: the codec's encode, or with stochastic rounding
+// the same scaled deviation (f - w_i ref) 2^k rounded with the node pair's random bits h.
+template <class S>
+__device__ __forceinline__ S enc_pop(const KParams &kp, typename Codec<S>::R f, typename Codec<S>::R wref,
+                                     typename Codec<S>::R scale, int64_t k, int i, uint32_t h)
+{
+    if constexpr (IsDev<S>::value) {
+        if (kp.sr) return sr_one<S>(__fmul_rn(__fsub_rn(f, wref), scale), sr_bits(h, i), (int)(k & 1));
+    }
+    return Codec<S>::enc(f, wref, scale);
+}
+
 // ------------------------------------------------------------- EOS ---------
 // Sec. 2: psi = sqrt(2 (p_EOS - rho c_s^2)/G); van der Waals (Sec. 3) or Carnahan-Starling.
 template <class R>
@@ -345,9 +418,10 @@ __device__ __forceinline__ void store_node(const KParams &kp, int x, int y, cons
         kp.ref_dst[k] = float(rho);
     }
     const R scale = cst<R>(kp).scale;
+    const uint32_t h = IsDev<S>::value && kp.sr ? sr_hash((uint32_t)(k >> 1), kp.sr_seed) : 0u;
 #pragma unroll
     for (int i = 0; i < 9; ++i) {
-        if constexpr (IsDev<S>::value) Bp[i * kp.plane + k] = Codec<S>::enc(fb[i], __fmul_rn(w_<R>(i), ref), scale);
+        if constexpr (IsDev<S>::value) Bp[i * kp.plane + k] = enc_pop<S>(kp, fb[i], __fmul_rn(w_<R>(i), ref), scale, k, i, h);
         else Bp[i * kp.plane + k] = Codec<S>::enc(fb[i], R(0), scale);
     }
 }

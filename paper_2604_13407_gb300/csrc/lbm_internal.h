@@ -42,6 +42,8 @@ struct KParams {
     int force_mode;  // 0 constant, 1 (rho - rho_g) g, 2 field
     int var_tau;     // 1: tau(rho) from the linear nu(rho) interpolation
     int per_node_ref;
+    int sr;            // FP16/BF16 storage: 1 stochastic rounding, 0 to nearest
+    uint32_t sr_seed;  // random-bit seed of this step (a hash of the step count)
     // EOS: p = K (rho RT g(rho) - a rho^2); psi = sqrt(two_over_G (p - rho/3))
     double eos_a, eos_b, eos_RT, eos_K, two_over_G;
     double eos_R, eos_T;  // raw R and T (FP64 path evaluates (rho R) T like a plain formula)

@@ -16,8 +16,8 @@ the oracle hours).  Prints one JSON line per configuration.
   against FP64.
 * C3, annular shear flow (Sec. 3.2), 1024 x 1024: resting inner cylinder r < 128, outer
   cylinder r > 480 moving tangentially at u_w = 0.01, both through interpolated (Bouzidi)
-  links; liquid annulus 200 < r < 320 in gas; 500k steps; FP32 against FP16 and BF16
-  deviation storage (per-node reference).  The run proceeds in chunks and records the first
+  links; liquid annulus 200 < r < 320 in gas; 500k steps; FP32 against FP16 (rounded to
+  nearest and stochastically) and BF16 deviation storage (per-node reference).  The run proceeds in chunks and records the first
   chunk that ends with a non-finite field: interpolated bounce-back does not conserve mass
   where the wall holds a density gradient (the adsorbed gas layer), and the heavy ring
   between lighter gas is the Rayleigh-Taylor-unstable layout that Sec. 3.2 avoids.  The
@@ -27,7 +27,7 @@ the oracle hours).  Prints one JSON line per configuration.
   in gas at the density in equilibrium with it (see _vapour_density; in Maxwell gas the
   droplet evaporates within 40k steps); relaxed without gravity, then buoyant gravity
   (rho - rho_g) g with |g| = 2e-6, rho_g that ambient density; 300k steps; original and
-  improved scheme, FP32 and FP16; FP64 reductions of mass, the momentum handed to the walls
+  improved scheme, FP32 and FP16 (rounded to nearest and stochastically); FP64 reductions of mass, the momentum handed to the walls
   (drag) and U_c, and the droplet's equivalent radius and centre line.
 
     python -m tests.baseline_configs [--configs c2,c3,c4] [--scale S] [--prefix P] [--force F]
@@ -194,8 +194,9 @@ def c3(lbm, steps=500000, prefix=2000, n=1024, chunk=25000, compare_at=25000):
     out = {"config": "C3", "lattice": "%dx%d" % (n, n), "steps": steps, "chunk": chunk,
            "geometry": "resting cylinder r < 128, cylinder r > 480 moving at 0.01, interpolated links; "
                        "liquid annulus 200 < r < 320"}
-    precs = (("f32", lbm.F32, {}), ("f16dev", lbm.F16DEV, {"per_node_ref": 1}),
-             ("bf16dev", lbm.BF16DEV, {"per_node_ref": 1}))
+    precs = (("f32", lbm.F32, {}), ("f16dev_nearest", lbm.F16DEV, {"per_node_ref": 1, "storage_rounding": 0}),
+             ("f16dev_stochastic", lbm.F16DEV, {"per_node_ref": 1, "storage_rounding": 1}),
+             ("bf16dev_stochastic", lbm.BF16DEV, {"per_node_ref": 1, "storage_rounding": 1}))
     o = _oracle_prefix(case, prefix)
     out["oracle_mass_drift_%d_steps" % prefix] = float(o.moments()[0][fluid].sum() / rho0[fluid].sum() - 1.0)
     for name, prec, kw in precs:
@@ -216,7 +217,7 @@ def c3(lbm, steps=500000, prefix=2000, n=1024, chunk=25000, compare_at=25000):
         if blew is None:
             out[name]["glups"] = _glups(s, int(fluid.size), 2000)
         s.close()
-    for name in ("f16dev", "bf16dev"):
+    for name in ("f16dev_nearest", "f16dev_stochastic", "bf16dev_stochastic"):
         if kept[name] is not None and kept["f32"] is not None:
             eu, er = _moment_err(kept[name], kept["f32"], fluid)
             out["%s_vs_f32_%d_steps" % (name, compare_at)] = {"e_u": eu, "e_rho": er}
@@ -254,7 +255,9 @@ def c4(lbm, steps=300000, prefix=1000, relax=20000, nx=512, ny=4096, g=2e-6, rad
     # the oracle prefix, with gravity from the start
     case = GC.Case("c4", mk(-g, 1), rho0, prefix)
     o = _oracle_prefix(case, prefix)
-    for name, prec, kw in (("f32", lbm.F32, {}), ("f16dev", lbm.F16DEV, {"per_node_ref": 1})):
+    c4_precs = (("f32", lbm.F32, {}), ("f16dev_nearest", lbm.F16DEV, {"per_node_ref": 1, "storage_rounding": 0}),
+                ("f16dev_stochastic", lbm.F16DEV, {"per_node_ref": 1, "storage_rounding": 1}))
+    for name, prec, kw in c4_precs:
         s = GC.run_gpu(case, prec, **kw)
         eu, er = _field_err(s, o)
         out["%s_vs_oracle_%d_steps" % (name, prefix)] = {"e_u": eu, "e_rho": er, "kernel": ["auto", "two_pass", "fused"][s.kernel_in_use]}
@@ -263,7 +266,7 @@ def c4(lbm, steps=300000, prefix=1000, relax=20000, nx=512, ny=4096, g=2e-6, rad
     xs = np.arange(nx)[None, :]
     ys = np.arange(ny)[:, None]
     for scheme in (0, 1):
-        for name, prec, kw in (("f32", lbm.F32, {}), ("f16dev", lbm.F16DEV, {"per_node_ref": 1})):
+        for name, prec, kw in c4_precs:
             key = "%s_%s" % ("original" if scheme == 0 else "improved", name)
             t0 = time.time()
             s = lbm.Simulation(GC.gpu_params(mk(0.0, scheme), prec, **kw))
@@ -299,9 +302,10 @@ def c4(lbm, steps=300000, prefix=1000, relax=20000, nx=512, ny=4096, g=2e-6, rad
         out[key + "_momentum_balance"] = abs(last["drag_y"] - last["force_y"]) / abs(last["force_y"])
         out[key + "_U_c"] = last["U_c"]
     for sch in ("original", "improved"):
-        a, b = out.get(sch + "_f16dev_U_c"), out.get(sch + "_f32_U_c")
-        if a is not None and b is not None:
-            out[sch + "_f16dev_vs_f32_U_c"] = abs(a - b) / abs(b)
+        for name in ("f16dev_nearest", "f16dev_stochastic"):
+            a, b = out.get("%s_%s_U_c" % (sch, name)), out.get(sch + "_f32_U_c")
+            if a is not None and b is not None:
+                out["%s_%s_vs_f32_U_c" % (sch, name)] = abs(a - b) / abs(b)
     return out
 
 

@@ -41,7 +41,7 @@ def test_struct_layout_matches():
 
 
 @pytest.mark.parametrize("field,value", [("nx", 0), ("ny", 65536), ("tau_l", 0.5), ("G", 0.5), ("Lambda", 0.0),
-                                         ("precision", 7), ("eos", 3), ("kernel", 9)])
+                                         ("precision", 7), ("eos", 3), ("kernel", 9), ("storage_rounding", 2)])
 def test_create_rejects_invalid_parameters(field, value):
     p = lbm.default_params(**{field: value})
     with pytest.raises(lbm.LbmError) as e:
