@@ -76,6 +76,9 @@ def converge(sim, chunk, tol=TOL, max_chunks=400, log=None):
         sim.set_state(S)
         steps += chunk + 1
         _, u, v = sim.moments()
+        if not (np.all(np.isfinite(u)) and np.all(np.isfinite(v))):
+            change = float("nan")
+            break
         if prev_u is not None:
             change = max(np.abs(u - prev_u[0]).max(), np.abs(v - prev_u[1]).max()) / max(np.abs(u).max(), np.abs(v).max())
             if change < tol:
