@@ -503,8 +503,8 @@ def main():
             if name == "f16dev_node_ref_nearest":
                 variants[name]["note"] = "stored deviations rounded to nearest (storage_rounding = 0)"
             if name == "f16dev_global_ref":
-                variants[name]["note"] = ("deviations from one reference density: not accurate at this density "
-                                          "ratio (O(1) error); bytes and speed only")
+                variants[name]["note"] = ("deviations from one reference density, stochastically rounded: about "
+                                          "5e-2 of max |u| on the two-phase channel (16x the per-node mode)")
             if prec == "f64":
                 # FP64-ALU bound: ncu shows the FP64 pipe busy and DRAM nearly idle (k_fused_f64 profile)
                 variants[name]["bound"] = "fp64 alu"
