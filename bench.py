@@ -36,7 +36,7 @@ BYTES = {"f64": 144, "f32": 72, "f16dev": 36, "bf16dev": 36}
 # f16dev: the per-node reference mode), scaled to a launch by the updates it makes.
 # Valid for the kernel as captured; an entry is removed when the kernel changes until it is captured
 # again (the line then reports traffic null).
-TRAFFIC_PER_UPDATE = {"f32": 73.85, "f16dev": 44.0}
+TRAFFIC_PER_UPDATE = {"f32": 73.86, "f16dev": 43.93}
 HBM_FALLBACK = 6800.0
 
 

@@ -250,10 +250,13 @@ __device__ __forceinline__ R bounce(const KParams &kp, int x, int y, const At &a
             const int64_t wk = (int64_t)wy * kp.nx + wx;
             const R uwx = R(kp.wall_u[wk]);
             const R uwy = R(kp.wall_u[(int64_t)kp.nx * kp.ny + wk]);
-            R rho_w = R(0);
+            // a wall at rest adds nothing (mw = +-0, which leaves the sum below unchanged)
+            if (uwx != R(0) || uwy != R(0)) {
+                R rho_w = R(0);
 #pragma unroll
-            for (int k = 0; k < 9; ++k) rho_w += at(k, x, y);
-            mw = R(2) * w_<R>(o) * rho_w * (R(ex_(i)) * uwx + R(ey_(i)) * uwy) * R(3);
+                for (int k = 0; k < 9; ++k) rho_w += at(k, x, y);
+                mw = R(2) * w_<R>(o) * rho_w * (R(ex_(i)) * uwx + R(ey_(i)) * uwy) * R(3);
+            }
         }
     }
     R q = R(0.5);

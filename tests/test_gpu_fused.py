@@ -61,7 +61,7 @@ def test_fused_with_solid_walls_matches_oracle(geom):
     rho; FP64 contexts keep the two-pass kernels for such geometry."""
     c = WALL_GEOMS[geom]
     o = GC.run_oracle(c)
-    g = GC.run_gpu(c, lbm.F32, lbm.KERNEL_AUTO)
+    g = GC.run_gpu(c, lbm.F32, lbm.KERNEL_FUSED)
     assert g.kernel_in_use == lbm.KERNEL_FUSED
     e_rho, e_u = GC.field_errors(g, o, c.solid)
     print("fused FP32 %s: e_u %.3e e_rho %.3e" % (geom, e_u, e_rho))
@@ -186,3 +186,26 @@ def test_full_size_sampled_nodes_match_oracle(prec, tol):
         s.step(1)
         ref = s.get_state()[:, 2, 2]
         assert np.abs(a - ref).max() < tol * np.abs(ref).max(), (a, ref)
+
+
+@pytest.mark.parametrize("nx,ny,walls_x,geom,want", [
+    (256, 256, False, None, lbm.KERNEL_TWO_PASS), (512, 512, False, None, lbm.KERNEL_FUSED),
+    (2048, 2048, False, None, lbm.KERNEL_FUSED), (256, 2048, True, None, lbm.KERNEL_TWO_PASS),
+    (512, 4096, True, None, lbm.KERNEL_FUSED), (512, 512, False, "band", lbm.KERNEL_TWO_PASS),
+    (2048, 2048, False, "band", lbm.KERNEL_FUSED), (1024, 1024, False, "q", lbm.KERNEL_TWO_PASS)])
+def test_auto_kernel_choice(nx, ny, walls_x, geom, want):
+    """KERNEL_AUTO takes the one-pass kernel where it was measured faster (FP32): larger
+    lattices, and solid or interpolated walls only on lattices large enough for the bulk to
+    outweigh the walls' per-link work; FP16 follows the same rule."""
+    for prec in (lbm.F32, lbm.F16DEV):
+        p = lbm.default_params(nx=nx, ny=ny, periodic_x=0 if walls_x else 1, periodic_y=1, precision=prec,
+                               per_node_ref=1, storage_scale_log2=18 if prec == lbm.F16DEV else 0)
+        s = lbm.Simulation(p)
+        if geom == "band":
+            s.set_geometry(I.oblique_band_walls(nx))
+        elif geom == "q":
+            solid = np.zeros((ny, nx), np.uint8)
+            solid[:, :2] = 1
+            s.set_geometry(solid, None, np.full((8, ny, nx), 0.5))
+        assert s.kernel_in_use == want, (nx, ny, geom, prec, s.kernel_in_use)
+        s.close()
