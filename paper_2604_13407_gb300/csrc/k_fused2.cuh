@@ -543,7 +543,8 @@ __global__ void __launch_bounds__(32 * (NW + 1), LBM_FUSED2_MINB) k_fused2(KPara
 #undef LBM_PULL_PAIR
 
 // Grid shape: about CTAS_PER_SM CTAs per SM, each a strip of rows no shorter than ROWS_L2
-// rows when both population buffers together take at most L2_STATE_MB, else ROWS_HBM rows.
+// rows when both population buffers together take at most L2_STATE_MB, else ROWS_HBM rows
+// (shortened, down to ROWS_L2, where that would leave fewer than MIN_CTAS_PER_SM per SM).
 #ifndef LBM_FUSED2_CTAS_PER_SM
 #define LBM_FUSED2_CTAS_PER_SM 16
 #endif
@@ -555,6 +556,9 @@ __global__ void __launch_bounds__(32 * (NW + 1), LBM_FUSED2_MINB) k_fused2(KPara
 #endif
 #ifndef LBM_FUSED2_L2_STATE_MB
 #define LBM_FUSED2_L2_STATE_MB 64
+#endif
+#ifndef LBM_FUSED2_MIN_CTAS_PER_SM
+#define LBM_FUSED2_MIN_CTAS_PER_SM 4
 #endif
 
 template <class S, int NW, int RING>
@@ -571,7 +575,12 @@ struct Fused2 {
         // segments re-read 3 halo rows; a lattice whose two population buffers fit in L2 reads
         // them from L2, so it may be cut into short segments (more CTAs), a larger one not
         const double state_bytes = 2.0 * 9.0 * (double)kp.plane * sizeof(S);
-        const int min_rows = state_bytes <= LBM_FUSED2_L2_STATE_MB * 1048576.0 ? LBM_FUSED2_ROWS_L2 : LBM_FUSED2_ROWS_HBM;
+        int min_rows = state_bytes <= LBM_FUSED2_L2_STATE_MB * 1048576.0 ? LBM_FUSED2_ROWS_L2 : LBM_FUSED2_ROWS_HBM;
+        // but not so long that the grid holds fewer than MIN_CTAS_PER_SM CTAs per SM: a
+        // mid-size lattice (1024^2 FP32: 5 strips x 64 segments of 16 rows = 2 CTAs per SM) is
+        // then latency bound, one CTA walking its rows with nothing to hide the waits
+        const int64_t occ_rows = (int64_t)kp.ny * strips / ((int64_t)LBM_FUSED2_MIN_CTAS_PER_SM * sms);
+        if (min_rows > occ_rows) min_rows = occ_rows > LBM_FUSED2_ROWS_L2 ? (int)occ_rows : LBM_FUSED2_ROWS_L2;
         const int max_seg = kp.ny / min_rows > 0 ? kp.ny / min_rows : 1;
         if (nseg > max_seg) nseg = max_seg;
         if (nseg < 1) nseg = 1;

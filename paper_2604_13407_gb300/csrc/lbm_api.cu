@@ -272,14 +272,14 @@ static bool fused_possible(const lbm_ctx *c)
 // thread per node, hide latency better: periodic 256^2 7.1 us against 8.8, 512^2 12.4
 // against 10.1; a 256-wide channel with x walls 23.5 against 29.5 (two strips, the second
 // 16 columns wide); 512 x 4096 84 against 57.  Solid bands: 512^2 19 against 22, 1024^2 55
-// against 58, 2048^2 251 against 113.  Interpolated and moving walls, whose per-link reads
+// against 46, 2048^2 251 against 113.  Interpolated and moving walls, whose per-link reads
 // of link fractions and wall velocities sit on the one-pass kernel's serial path: annulus
 // 1024^2 51 against 117, 2048^2 202 against 240.
 static bool auto_prefers_fused(const lbm_ctx *c)
 {
     const int64_t n = (int64_t)c->p.nx * c->p.ny;
     if (c->q || c->wall_u) return n > (int64_t(1) << 22);
-    if (c->solid) return n > (int64_t(1) << 20);
+    if (c->solid) return n >= (int64_t(1) << 20);
     return (n >= (int64_t(1) << 18) && c->p.nx >= 512) || n >= (int64_t(1) << 21);
 }
 
