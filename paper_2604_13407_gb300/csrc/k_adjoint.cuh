@@ -39,6 +39,29 @@ __device__ __forceinline__ bool wall_link(const KParams &kp, int x, int y, int i
     return false;
 }
 
+// Walls among the eight neighbours of (x, y): bit i set when x + e_i is a solid node or lies
+// beyond a non-periodic edge.  One set of global solid-flag reads per node serves the pull
+// (population i comes from x - e_i = x + e_opp(i)), lambda_{t+1}, the objective and the wall
+// psi terms.
+__device__ __forceinline__ unsigned wall_mask(const KParams &kp, int x, int y)
+{
+    unsigned wm = 0;
+#pragma unroll
+    for (int i = 1; i < 9; ++i) {
+        int64_t kn;
+        if (wall_link(kp, x, y, i, kn)) wm |= 1u << i;
+    }
+    return wm;
+}
+
+// Row-major pitched index of the fluid neighbour x + e_i (wrapped along periodic directions).
+__device__ __forceinline__ int64_t neighbour_k(const KParams &kp, int x, int y, int i)
+{
+    int xn = x + ex_(i), yn = y + ey_(i);
+    wrap_xy(kp, xn, yn);
+    return (int64_t)yn * kp.pitch + xn;
+}
+
 // Objective weights W_i(x) at a fluid node (before the 1/n of the time average);
 // inv_nf = 1 / number of fluid nodes in the arithmetic type.
 template <class R>
@@ -48,18 +71,18 @@ __device__ __forceinline__ R objective_weight(int objective, int i, bool wall_ah
     return R(ex_(i)) * inv_nf;
 }
 
-// lambda_{t+1} of the nine populations of fluid node (x, y).
+// lambda_{t+1} of the nine populations of fluid node (x, y); wm its wall_mask.
 template <class R>
-__device__ __forceinline__ void lambda_at(const KParams &kp, const AdjArgs &aa, int x, int y, R wscale, R inv_nf,
-                                          R (&lam)[9])
+__device__ __forceinline__ void lambda_at(const KParams &kp, const AdjArgs &aa, int x, int y, unsigned wm, R wscale,
+                                          R inv_nf, R (&lam)[9])
 {
     const int64_t k = (int64_t)y * kp.pitch + x;
     const R *g = static_cast<const R *>(aa.g_in);
     const R *c = static_cast<const R *>(aa.c_in);
 #pragma unroll
     for (int i = 0; i < 9; ++i) {
-        int64_t kn = k;
-        const bool wall = (i != 0) && wall_link(kp, x, y, i, kn);
+        const bool wall = (i != 0) && ((wm >> i) & 1u);
+        const int64_t kn = (i == 0 || wall) ? k : neighbour_k(kp, x, y, i);
         R v = wscale * objective_weight<R>(aa.objective, i, wall, inv_nf);
         if (g != nullptr) {
             if (wall) v += g[opp_(i) * kp.plane + k] + c[k];
@@ -118,8 +141,10 @@ __device__ __forceinline__ void block_add(const R (&v)[N], double *part, int fir
 {
     __shared__ double red[kRowThreads / 32][N];
     double w[N];
+    // a quantity that is zero on every lane of the warp (the wall terms away from walls) sums
+    // to exactly zero: skip its shuffles
 #pragma unroll
-    for (int k = 0; k < N; ++k) w[k] = warp_sum_r(v[k]);
+    for (int k = 0; k < N; ++k) w[k] = __any_sync(0xffffffffu, v[k] != R(0)) ? warp_sum_r(v[k]) : 0.0;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     if (lane == 0)
 #pragma unroll
@@ -160,12 +185,25 @@ __global__ void __launch_bounds__(kRowThreads) k_adj1(KParams kp, AdjArgs aa)
     const R inv_nf = R(aa.inv_nfluid);
     if (x < kp.nx && !node_is_solid(kp, node)) {
         const Consts<R> &cc = cst<R>(kp);
+        const unsigned wm = wall_mask(kp, x, y);
         R lam[9];
-        lambda_at<R>(kp, aa, x, y, R(aa.w_scale), inv_nf, lam);
+        lambda_at<R>(kp, aa, x, y, wm, R(aa.w_scale), inv_nf, lam);
 
-        // ---- forward quantities at this node
+        // ---- forward quantities at this node: the pull of Eq. (lbe.str) with half-way walls
+        // (the only walls the adjoint accepts): f_i = A_o(x) + 0 when x - e_i is a wall, as
+        // the forward step's bounce-back rule evaluates it
         R f[9];
-        pull_node<R>(kp, x, y, GlobalAt<S>{kp}, f, (R *)nullptr);
+        f[0] = load_pop<S>(kp, 0, x, y);
+#pragma unroll
+        for (int i = 1; i < 9; ++i) {
+            if ((wm >> opp_(i)) & 1u) {
+                f[i] = load_pop<S>(kp, opp_(i), x, y) + R(0);
+            } else {
+                int xs = x - ex_(i), ys = y - ey_(i);
+                wrap_xy(kp, xs, ys);
+                f[i] = load_pop<S>(kp, i, xs, ys);
+            }
+        }
         const R rho = density<R>(f);
         const R jx = ((f[1] - f[3]) + (f[5] - f[6])) + (f[8] - f[7]);
         const R jy = ((f[2] - f[4]) + (f[5] + f[6])) - (f[7] + f[8]);
@@ -176,8 +214,7 @@ __global__ void __launch_bounds__(kRowThreads) k_adj1(KParams kp, AdjArgs aa)
             R wall_y = R(0), wall_x = R(0);
 #pragma unroll
             for (int i = 1; i < 9; ++i) {
-                int xs = x - ex_(i), ys = y - ey_(i);
-                const bool wall = !wrap_xy(kp, xs, ys) || (kp.solid != nullptr && kp.solid[(int64_t)ys * kp.nx + xs] != 0);
+                const bool wall = (wm >> opp_(i)) & 1u;
                 if (wall) {
                     wall_x += R(ex_(i)) * f[i];
                     wall_y += R(ey_(i)) * f[i];
@@ -302,10 +339,8 @@ __global__ void __launch_bounds__(kRowThreads) k_adj1(KParams kp, AdjArgs aa)
         // walls in the stencil carry psi(rho_s; T, G)
         R dpsi_s = R(0);
 #pragma unroll
-        for (int i = 1; i < 9; ++i) {
-            int64_t kn;
-            if (wall_link(kp, x, y, i, kn)) dpsi_s += omega_<R>(i) * (R(ex_(i)) * dSx + R(ey_(i)) * dSy);
-        }
+        for (int i = 1; i < 9; ++i)
+            if ((wm >> i) & 1u) dpsi_s += omega_<R>(i) * (R(ex_(i)) * dSx + R(ey_(i)) * dSy);
         if (dpsi_s != R(0)) {
             R prs, pTs;
             p_eos_derivs<R>(kp, cc.rho_s, prs, pTs);
@@ -387,7 +422,7 @@ __global__ void __launch_bounds__(kRowThreads) k_adj_lambda(KParams kp, AdjArgs 
 #pragma unroll
         for (int i = 0; i < 9; ++i) lam[i] = R(0);
     } else {
-        lambda_at<R>(kp, aa, x, y, R(0), R(aa.inv_nfluid), lam);
+        lambda_at<R>(kp, aa, x, y, wall_mask(kp, x, y), R(0), R(aa.inv_nfluid), lam);
     }
 #pragma unroll
     for (int i = 0; i < 9; ++i) out[i * n + node] = double(lam[i]);
