@@ -45,6 +45,12 @@ WIDTH_ALIGNED = 181
 N_OBLIQUE = 256
 EQUILIBRATION_STEPS = 20000
 TOL = 1e-7
+START_FROM_REST = False  # restart the forced stage from u = 0 instead of the theory profile
+# initial slab at the model's own coexistence densities (Eq. (1), mechanical stability) instead of
+# the Maxwell ones; at epsilon = 0 the model's gas is 4x thinner than Maxwell's, and on the 256^2
+# oblique lattice at tau = 0.8 the transient from the Maxwell densities reaches |u| = 0.66 and
+# ends in NaN (oracle and GPU alike) within 600 steps
+INIT_COEXISTENCE = False
 
 # Table 1 as printed (Err x 100): "epsilon geometry" -> original tau 0.8, original tau 1.5,
 # improved tau 0.8, improved tau 1.5
@@ -204,7 +210,11 @@ def run_oblique(backend, eps, t_r, tau, scheme, n=N_OBLIQUE, tol=TOL, log=None, 
                               scheme=scheme, tau_l=tau, tau_g=tau)
     solid = I.oblique_band_walls(n)
     sim = backend.make(mk(0.0), solid)
-    sim.init_fields(np.where(solid == 1, rg, I.oblique_slab(n, rl, rg, n // 2)))
+    g0, l0 = rg, rl
+    if INIT_COEXISTENCE:
+        op0 = mk(0.0)
+        g0, l0, _ = A.mechanical_stability(eps, op0.eos, op0.a, op0.b, op0.R, op0.T, op0.K_eos)
+    sim.init_fields(np.where(solid == 1, rg, I.oblique_slab(n, l0, g0, n // 2)))
     sim.step(EQUILIBRATION_STEPS)
     rho, _, _ = sim.moments()
     op = mk(f)
@@ -213,7 +223,7 @@ def run_oblique(backend, eps, t_r, tau, scheme, n=N_OBLIQUE, tol=TOL, log=None, 
     ub0 = np.zeros(n)
     ub0[idx] = A.poiseuille_theory(rho[0, idx], F_DRIVE, nu_fn(op), spacing=spacing)
     alpha = (np.arange(n)[None, :] - np.arange(n)[:, None]) % n
-    ub = ub0[alpha]
+    ub = ub0[alpha] if not START_FROM_REST else np.zeros_like(ub0[alpha])
     sim = backend.make(op, solid)
     sim.init_fields(rho, ub / math.sqrt(2.0), ub / math.sqrt(2.0))
     nu = (tau - 0.5) / 3.0
@@ -251,15 +261,26 @@ def main():
     ap.add_argument("--eps", type=float, nargs="*", default=[c[0] for c in CASES])
     ap.add_argument("--log", action="store_true", help="per-chunk change on stderr")
     ap.add_argument("--equilibration", type=int, default=None, help="steps without force")
+    ap.add_argument("--tau", type=float, nargs="*", default=None, help="only these relaxation times")
+    ap.add_argument("--from-rest", action="store_true",
+                    help="start the forced stage from rest (oblique) instead of the theory profile")
+    ap.add_argument("--init-coexistence", action="store_true",
+                    help="initial oblique slab at the model's coexistence densities instead of Maxwell's")
     args = ap.parse_args()
     if args.equilibration is not None:
         globals()["EQUILIBRATION_STEPS"] = args.equilibration
+    if args.from_rest:
+        globals()["START_FROM_REST"] = True
+    if args.init_coexistence:
+        globals()["INIT_COEXISTENCE"] = True
     import torch
     torch.cuda.set_device(0)
     from paper_2604_13407_gb300 import lbm
     backend = GpuBackend({"f64": lbm.F64, "f32": lbm.F32}[args.precision])
     backend.name = args.precision
     taus = (1.5,) if args.quick else TAUS
+    if args.tau:
+        taus = tuple(args.tau)
     geoms = ("aligned", "oblique") if args.geometry == "both" else (args.geometry,)
     for geom in geoms:
         for eps, t_r in CASES:
