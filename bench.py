@@ -168,7 +168,8 @@ def job_updates(n, steps, world):
 
 def e2e_glups(n, precision, steps, rho_host, per_node_ref=1):
     """Same metric through the public API with host buffers: H2D of the initial density
-    (pinned), `steps` steps, D2H of rho, ux, uy; all inside the timed region."""
+    (pinned), `steps` steps, D2H of rho, ux, uy into pinned host buffers; all inside the
+    timed region."""
     import torch
     from paper_2604_13407_gb300 import lbm
     sim = make_sim(n, precision, per_node_ref=per_node_ref)
@@ -177,11 +178,12 @@ def e2e_glups(n, precision, steps, rho_host, per_node_ref=1):
     h = pinned.numpy()
     sim.init_fields(h)
     sim.step(2)
+    sim.moments(out=out)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     sim.init_fields(h)
     sim.step(steps)
-    r, u, v = sim.moments()
+    sim.moments(out=out)  # D2H of rho, ux, uy into pinned host memory (synchronises)
     torch.cuda.synchronize()
     t = time.perf_counter() - t0
     sim.close()

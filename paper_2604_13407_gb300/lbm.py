@@ -237,10 +237,25 @@ class Simulation:
 
     # ---- read-back
     def moments(self, out=None):
-        """(rho, ux, uy) as [ny, nx] numpy arrays, or into three torch CUDA tensors."""
+        """(rho, ux, uy) as [ny, nx] numpy arrays, or into `out`: three torch CUDA tensors
+        (device copies), or three host buffers of nx * ny doubles -- numpy arrays or torch
+        CPU tensors, pinned ones for full-speed transfers."""
         if out is not None:
-            r, u, v = out
-            self._check(self.lib.lbm_get_moments(self._h, r.data_ptr(), u.data_ptr(), v.data_ptr(), 1))
+            if all(_is_torch_cuda(a) for a in out):
+                r, u, v = out
+                self._check(self.lib.lbm_get_moments(self._h, r.data_ptr(), u.data_ptr(), v.data_ptr(), 1))
+                return out
+            ptrs = []
+            for a in out:
+                if hasattr(a, "data_ptr"):  # torch CPU tensor
+                    if a.dtype != __import__("torch").float64 or not a.is_contiguous() or a.numel() != self.n:
+                        raise ValueError("expected a contiguous float64 tensor of %d elements" % self.n)
+                    ptrs.append(a.data_ptr())
+                else:
+                    if a.dtype != np.float64 or not a.flags["C_CONTIGUOUS"] or a.size != self.n:
+                        raise ValueError("expected a contiguous float64 array of %d elements" % self.n)
+                    ptrs.append(a.ctypes.data)
+            self._check(self.lib.lbm_get_moments(self._h, ptrs[0], ptrs[1], ptrs[2], 0))
             return out
         r = np.zeros((self.ny, self.nx))
         u = np.zeros((self.ny, self.nx))

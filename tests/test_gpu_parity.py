@@ -212,6 +212,23 @@ def test_save_load_roundtrip_bitwise():
         assert np.array_equal(sim.get_state(), after)
 
 
+def test_moments_into_host_buffers():
+    """moments(out=...) with numpy arrays or (pinned) torch CPU tensors gives the same values
+    as the arrays it allocates itself."""
+    import torch
+    c = CASES["droplet"]
+    sim = GC.run_gpu(c, lbm.F32, steps=10)
+    ref = sim.moments()
+    n = sim.n
+    for bufs in ([np.empty(n) for _ in range(3)], [torch.empty(n, dtype=torch.float64).pin_memory() for _ in range(3)]):
+        got = sim.moments(out=bufs)
+        for a, b in zip(got, ref):
+            a = a.numpy() if hasattr(a, "numpy") else a
+            assert np.array_equal(a.reshape(b.shape), b)
+    with pytest.raises(ValueError):
+        sim.moments(out=[np.empty(n, dtype=np.float32) for _ in range(3)])
+
+
 def test_nan_is_reported():
     c = CASES["droplet"]
     sim = GC.run_gpu(c, lbm.F32, steps=1)
