@@ -270,22 +270,27 @@ def geometry_cases():
            I.droplet(nx, ny, RHO_L, RHO_G, 40.0, cx, cy, periodic_x=False, periodic_y=True), None, None, None)
 
 
-def geometry_throughput(hbm, steps=2000, warmup=20):
-    """GLUPS of the one-pass step on the geometry_cases lattices (CUDA events on the
-    launching stream).  Bytes per update: the population read and write of the storage
-    type, plus the node's solid flag where there is a mask; interpolated-link distances and
-    wall velocities are read only at wall links.  The two smaller lattices' state fits in
-    L2 (and the step is bound by latency, not by HBM), so their fraction of the HBM copy
-    bandwidth is reported for comparison only."""
+def geometry_throughput(hbm, steps=2000, warmup=20, only=None, kernel=0, precs=("f32", "f16dev")):
+    """GLUPS of the step on the geometry_cases lattices (CUDA events on the launching
+    stream), with the kernel the automatic choice takes ("kernel" names it) unless `kernel`
+    asks for one.  Bytes per update (algorithmic): the population read and write of the
+    storage type, plus the node's solid flag where there is a mask; interpolated-link
+    distances and wall velocities are read only at wall links.  The two smaller lattices'
+    state fits in L2 (and the step is bound by latency, not by HBM), so their fraction of the
+    HBM copy bandwidth is reported for comparison only.  `only` restricts the run to one
+    case (for profiling)."""
     import torch
     from paper_2604_13407_gb300 import lbm
     out = {}
     for name, over, rho, solid, wall_u, q in geometry_cases():
-        for prec in ("f32", "f16dev"):
-            pid = lbm.F32 if prec == "f32" else lbm.F16DEV
+        if only is not None and name != only:
+            continue
+        for prec in precs:
+            pid = {"f64": lbm.F64, "f32": lbm.F32, "f16dev": lbm.F16DEV, "bf16dev": lbm.BF16DEV}[prec]
+            half = prec in ("f16dev", "bf16dev")
             p = lbm.default_params(precision=pid, scheme=1, T=T_07, rho_l=RHO_L, rho_g=RHO_G, rho_s=RHO_G,
                                    rho_ref=0.5 * (RHO_L + RHO_G), per_node_ref=1,
-                                   storage_scale_log2=18 if prec == "f16dev" else 0, **over)
+                                   storage_scale_log2=18 if prec == "f16dev" else 0, kernel=kernel, **over)
             s = lbm.Simulation(p, stream=torch.cuda.current_stream())
             if solid is not None:
                 s.set_geometry(solid, wall_u, q, None)
@@ -293,9 +298,9 @@ def geometry_throughput(hbm, steps=2000, warmup=20):
             nodes = over["nx"] * over["ny"]
             t = timed_steps(s, steps, warmup, False)
             g = nodes * steps / t / 1e9
-            b = BYTES[prec] + (8 if prec == "f16dev" else 0) + (1 if solid is not None else 0)
-            # two population buffers (and two reference planes for per-node FP16)
-            state_mb = (BYTES[prec] + (8 if prec == "f16dev" else 0)) * nodes / 1e6
+            b = BYTES[prec] + (8 if half else 0) + (1 if solid is not None else 0)
+            # two population buffers (and two reference planes for per-node 16-bit storage)
+            state_mb = (BYTES[prec] + (8 if half else 0)) * nodes / 1e6
             out["%s_%s" % (name, prec)] = {
                 "GLUPS": g, "us_per_step": 1e6 * t / steps, "bytes_per_update": b, "achieved_GBs": b * g,
                 "frac_of_hbm": b * g / hbm, "state_MB": state_mb, "steps": steps,
@@ -425,6 +430,11 @@ def main():
     ap.add_argument("--ref-sample", type=int, default=512)
     ap.add_argument("--e2e", type=int, default=1)
     ap.add_argument("--adjoint", type=int, default=1, help="also time the adjoint against the forward step")
+    ap.add_argument("--geometry-only", default=None,
+                    choices=("oblique_channel_512", "annulus_1024", "falling_droplet_512x4096"),
+                    help="time only this geometry-shaped lattice at --precision (one JSON line; for profiling)")
+    ap.add_argument("--kernel", default="auto", choices=("auto", "two_pass", "fused"),
+                    help="step kernel for --geometry-only")
     ap.add_argument("--adjoint-only", type=int, default=0,
                     help="time only the adjoint against the forward step (one JSON line; for profiling)")
     ap.add_argument("--oracle-sample", default=None, choices=sorted(ORACLE_SAMPLES),
@@ -437,6 +447,13 @@ def main():
         return
     if args.impl == "reference":
         return run_reference(args)
+    if args.geometry_only:
+        import torch
+        torch.cuda.set_device(0)
+        k = {"auto": 0, "two_pass": 1, "fused": 2}[args.kernel]
+        print(json.dumps({"geometry": geometry_throughput(peaks()[0], args.steps, args.warmup, args.geometry_only, k,
+                                                          (args.precision,))}))
+        return
     if args.adjoint_only:
         import torch
         from paper_2604_13407_gb300 import lbm
