@@ -218,6 +218,29 @@ struct StagedAt {
     }
 };
 
+// A wall link from its record (KParams::link: link fraction q, moving-wall coefficient c):
+// the bounce-back rule of `bounce` (Bouzidi interpolation, moving-wall term c rho_w with
+// rho_w the node's own density before the last collision), reading the populations from the
+// staged rows.  One 8-byte read per link replaces the separate reads of q, the wall velocity
+// and the solid flag of the second node.
+template <int I, class At>
+__device__ __forceinline__ float bounce_link(const At &at, int x, int y, float2 lk)
+{
+    constexpr int o = opp_(I);
+    const float fo = at(o, x, y);
+    const float q = lk.x;
+    float mw = 0.f;
+    if (lk.y != 0.f) {
+        float rho_w = 0.f;
+#pragma unroll
+        for (int k = 0; k < 9; ++k) rho_w += at(k, x, y);
+        mw = lk.y * rho_w;
+    }
+    if (q < 0.5f) return 2.f * q * fo + (1.f - 2.f * q) * at(o, x + ex_(I), y + ey_(I)) + mw;
+    if (q == 0.5f) return fo + mw;
+    return fo / (2.f * q) + (2.f * q - 1.f) / (2.f * q) * at(I, x, y) + mw / (2.f * q);
+}
+
 // Wall links of the pair (edges beyond a non-periodic side and solid nodes): the bounce-back
 // of the two-pass step (half-way, moving wall, interpolated), element by element.
 #define LBM_GEOM_LINK(I)                                                                                      \
@@ -231,7 +254,7 @@ struct StagedAt {
             const bool wall_ = yw_ || (!kp.periodic_x && (xs_ < 0 || xs_ >= nx)) || ((wsrc_ >> (e - ex_(I) + 1)) & 1); \
             if (wall_) {                                                                                      \
                 float v_;                                                                                     \
-                if (!kp.q && !kp.wall_u) {                                                                    \
+                if constexpr (GEOM == 1) {                                                                    \
                     /* half-way: the population that left the node toward the wall returns */                \
                     constexpr int o_ = opp_(I);                                                               \
                     v_ = Pair2<S>::load1(row[1] + o_ * W + e);                                                \
@@ -239,8 +262,10 @@ struct StagedAt {
                         v_ = __fmaf_rn(v_, kp.cf.inv_scale, __fmul_rn(w_<float>(o_), ref[1] ? ref[1][e] : kp.cf.rho_ref)); \
                     v_ = v_ + 0.f;                                                                            \
                 } else {                                                                                      \
+                    /* interpolated or moving walls: the link records exist (set_geometry) */                 \
                     const StagedAt<S, W> at_{kp, row[0], row[1], row[2], ref[0], ref[1], ref[2], e, xw + e, yw}; \
-                    v_ = bounce<float, I>(kp, xw + e, yw, at_, (float *)nullptr);                             \
+                    v_ = bounce_link<I>(at_, xw + e, yw,                                                      \
+                                        kp.link[(int64_t)(I - 1) * kp.plane + (int64_t)yw * kp.pitch + xw + e]); \
                 }                                                                                             \
                 if (e == 0) f_new[I].v.x = v_;                                                                \
                 else f_new[I].v.y = v_;                                                                       \
@@ -251,7 +276,10 @@ struct StagedAt {
 #ifndef LBM_FUSED2_MINB
 #define LBM_FUSED2_MINB 2  // CTAs per SM the register allocation must allow
 #endif
-template <class S, int NW, int RING, bool PERIODIC, class O, bool GEOM = false>
+// GEOM: 0 no solid nodes; 1 solid nodes with half-way links only; 2 also interpolated or
+// moving walls (through the wall-link records).  The half-way-only instantiation keeps the
+// link code out of the kernel.
+template <class S, int NW, int RING, bool PERIODIC, class O, int GEOM = 0>
 __global__ void __launch_bounds__(32 * (NW + 1), LBM_FUSED2_MINB) k_fused2(KParams kp, int seg_rows)
 {
     typedef FusedLayout2<S, NW, RING> L;
@@ -564,7 +592,7 @@ __global__ void __launch_bounds__(32 * (NW + 1), LBM_FUSED2_MINB) k_fused2(KPara
 template <class S, int NW, int RING>
 struct Fused2 {
     typedef FusedLayout2<S, NW, RING> L;
-    template <bool P, class O, bool GEOM = false>
+    template <bool P, class O, int GEOM = 0>
     static cudaError_t launch_one(const KParams &kp, cudaStream_t st)
     {
         cudaError_t e = ensure_smem_attribute(k_fused2<S, NW, RING, P, O, GEOM>, kp.device, (int)L::bytes(true));
@@ -595,7 +623,8 @@ struct Fused2 {
     static cudaError_t launch(const KParams &kp, cudaStream_t st)
     {
         // solid nodes, moving walls or interpolated links: the general-geometry instantiation
-        if (kp.solid || kp.q || kp.wall_u) return launch_one<false, RuntimeOpts, true>(kp, st);
+        if (kp.q || kp.wall_u) return launch_one<false, RuntimeOpts, 2>(kp, st);
+        if (kp.solid) return launch_one<false, RuntimeOpts, 1>(kp, st);
         if (kp.periodic_x && kp.periodic_y && kp.force_mode == 0 && !kp.var_tau) {
             if (IsDev<S>::value && kp.per_node_ref)
                 return kp.improved ? launch_one<true, Opts<1, 0, 0, 1>>(kp, st) : launch_one<true, Opts<0, 0, 0, 1>>(kp, st);

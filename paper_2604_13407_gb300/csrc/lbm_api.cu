@@ -33,6 +33,7 @@ struct lbm_ctx {
     uint8_t *solid = nullptr;
     double *wall_u = nullptr, *q = nullptr, *fext = nullptr;
     double *wall_rho = nullptr, *wall_psi = nullptr;  // per solid node virtual density, its psi
+    float2 *link = nullptr;             // wall-link records of the one-pass kernel (KParams::link)
     double *dacc = nullptr;             // diagnostics accumulators (9 doubles, 1 u64, 1 int)
     double *scratch = nullptr;          // host<->device staging for FP64 field copies
     size_t scratch_bytes = 0;
@@ -244,6 +245,7 @@ static void fill_constants(lbm_ctx *c)
     k.fext = c->fext;
     k.wall_rho = c->wall_rho;
     k.wall_psi = c->wall_psi;
+    k.link = c->link;
     k.err = c->derr;
 }
 
@@ -271,15 +273,15 @@ static bool fused_possible(const lbm_ctx *c)
 // walk down its rows dominates the one-pass kernel's time and the two-pass kernels, one
 // thread per node, hide latency better: periodic 256^2 7.1 us against 8.8, 512^2 12.4
 // against 10.1; a 256-wide channel with x walls 23.5 against 29.5 (two strips, the second
-// 16 columns wide); 512 x 4096 84 against 57.  Solid bands: 512^2 19 against 22, 1024^2 55
-// against 46, 2048^2 251 against 113.  Interpolated and moving walls, whose per-link reads
-// of link fractions and wall velocities sit on the one-pass kernel's serial path: annulus
-// 1024^2 51 against 117, 2048^2 202 against 240.
+// 16 columns wide); 512 x 4096 84 against 57.  Solid bands: 256^2 below, 512^2 19.1 against
+// 19.1 (FP16 26.5 against 21.9), 1024^2 55 against 41, 2048^2 251 against 100.  Interpolated
+// and moving walls, whose per-link work sits on the one-pass kernel's serial path: annulus
+// 1024^2 51 against 75, 2048^2 207 against 195 (FP16 258 against 211).
 static bool auto_prefers_fused(const lbm_ctx *c)
 {
     const int64_t n = (int64_t)c->p.nx * c->p.ny;
-    if (c->q || c->wall_u) return n > (int64_t(1) << 22);
-    if (c->solid) return n >= (int64_t(1) << 20);
+    if (c->q || c->wall_u) return n >= (int64_t(1) << 22);
+    if (c->solid) return n >= (int64_t(1) << 18);
     return (n >= (int64_t(1) << 18) && c->p.nx >= 512) || n >= (int64_t(1) << 21);
 }
 
@@ -297,7 +299,7 @@ static void free_all(lbm_ctx *c)
     if (!c) return;
     if (c->stream) cudaStreamSynchronize(c->stream);
     void *bufs[] = {c->pops[0], c->pops[1], c->refp[0], c->refp[1], c->psi, c->solid,
-                    c->wall_u, c->q, c->fext, c->wall_rho, c->wall_psi, c->dacc, c->scratch, c->derr};
+                    c->wall_u, c->q, c->fext, c->wall_rho, c->wall_psi, c->link, c->dacc, c->scratch, c->derr};
     for (void *b : bufs)
         if (b) cudaFree(b);
     adjoint_free(c->adj);
@@ -416,6 +418,61 @@ static lbm_status upload(lbm_ctx *c, T **dst, const T *src, size_t count, const 
     return LBM_OK;
 }
 
+// Wall-link records of the one-pass kernel (KParams::link), built on the host from the
+// geometry as given: for each fluid node x and pulled population i whose source x - e_i is a
+// wall (a solid node or beyond a non-periodic edge), the link fraction q of the outgoing
+// population o = opp(i) (1/2 without link fractions, and 1/2 where q < 1/2 but the second
+// node x + e_i is a wall too -- the same fallback as the two-pass step's bounce-back) and
+// the moving-wall coefficient 2 w_o (e_i . u_w) 3 of the wall node (0 beyond an edge).
+static lbm_status build_link_records(lbm_ctx *c, const uint8_t *solid, const double *wall_u, const double *q)
+{
+    static const int EX[9] = {0, 1, 0, -1, 0, 1, -1, -1, 1}, EY[9] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
+    static const int OPP[9] = {0, 3, 4, 1, 2, 7, 8, 5, 6};
+    static const double W[9] = {4.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 36, 1.0 / 36, 1.0 / 36, 1.0 / 36};
+    if (c->link) {
+        cudaStreamSynchronize(c->stream);
+        cudaFree(c->link);
+        c->link = nullptr;
+    }
+    if (!q && !wall_u) return LBM_OK;
+    const int nx = c->p.nx, ny = c->p.ny;
+    const int64_t n = (int64_t)nx * ny, pitch = c->pitch, plane = c->plane;
+    auto wall_at = [&](int x, int y, int64_t *node) -> bool {
+        if (x < 0 || x >= nx) {
+            if (!c->p.periodic_x) return true;
+            x = x < 0 ? x + nx : x - nx;
+        }
+        if (y < 0 || y >= ny) {
+            if (!c->p.periodic_y) return true;
+            y = y < 0 ? y + ny : y - ny;
+        }
+        *node = (int64_t)y * nx + x;
+        return solid && solid[*node] != 0;
+    };
+    std::vector<float2> h((size_t)(8 * plane), make_float2(0.5f, 0.0f));
+    for (int y = 0; y < ny; ++y)
+        for (int x = 0; x < nx; ++x) {
+            const int64_t node = (int64_t)y * nx + x, k = (int64_t)y * pitch + x;
+            if (solid && solid[node]) continue;
+            for (int i = 1; i < 9; ++i) {
+                int64_t wn = -1;
+                if (!wall_at(x - EX[i], y - EY[i], &wn)) continue;
+                const int o = OPP[i];
+                double qq = q ? q[(int64_t)(o - 1) * n + node] : 0.5;
+                int64_t bn;
+                if (qq < 0.5 && wall_at(x + EX[i], y + EY[i], &bn)) qq = 0.5;
+                double cw = 0.0;
+                if (wall_u && wn >= 0) cw = 2.0 * W[o] * (EX[i] * wall_u[wn] + EY[i] * wall_u[n + wn]) * 3.0;
+                h[(size_t)((i - 1) * plane + k)] = make_float2((float)qq, (float)cw);
+            }
+        }
+    CK(cudaMalloc((void **)&c->link, h.size() * sizeof(float2)), "link records");
+    CK(cudaMemcpyAsync(c->link, h.data(), h.size() * sizeof(float2), cudaMemcpyHostToDevice, c->stream),
+       "link records");
+    CK(cudaStreamSynchronize(c->stream), "link records");
+    return LBM_OK;
+}
+
 extern "C" lbm_status lbm_set_geometry(lbm_ctx *c, const uint8_t *solid, const double *wall_u, const double *q,
                                        const double *force_field)
 {
@@ -433,6 +490,7 @@ extern "C" lbm_status lbm_set_geometry(lbm_ctx *c, const uint8_t *solid, const d
     if ((s = upload(c, &c->wall_u, wall_u, 2 * n, "wall_u")) != LBM_OK) return s;
     if ((s = upload(c, &c->q, q, 8 * n, "q")) != LBM_OK) return s;
     if ((s = upload(c, &c->fext, force_field, 2 * n, "force_field")) != LBM_OK) return s;
+    if (c->p.precision != LBM_F64 && (s = build_link_records(c, solid, wall_u, q)) != LBM_OK) return s;
     CK(cudaStreamSynchronize(c->stream), "set_geometry");
     fill_constants(c);
     choose_kernel(c);

@@ -73,6 +73,11 @@ struct KParams {
     const double *fext;    // [2][ny*nx] or null
     const double *wall_rho;  // [ny*nx] virtual density of each solid node, or null (rho_s)
     const double *wall_psi;  // [ny*nx] psi of wall_rho, or null (psi_s)
+    // [8][ny][pitch] per fluid node and pulled population i = 1..8 whose source x - e_i is a
+    // wall: (q, c) with q the link fraction after the fallback of a missing second node, and
+    // c = 6 w_o (e_i . u_w) the moving-wall coefficient (mw = c rho_w); null without
+    // interpolated or moving walls.  Read by the one-pass kernel's wall links.
+    const float2 *link;
     int *err;              // device error word (0 = fine)
     Consts<double> cd;     // constants for FP64 arithmetic
     Consts<float> cf;      // constants for FP32 arithmetic
