@@ -264,8 +264,8 @@ __device__ __forceinline__ float bounce_link(const At &at, int x, int y, float2 
                 } else {                                                                                      \
                     /* interpolated or moving walls: the link records exist (set_geometry) */                 \
                     const StagedAt<S, W> at_{kp, row[0], row[1], row[2], ref[0], ref[1], ref[2], e, xw + e, yw}; \
-                    v_ = bounce_link<I>(at_, xw + e, yw,                                                      \
-                                        kp.link[(int64_t)(I - 1) * kp.plane + (int64_t)yw * kp.pitch + xw + e]); \
+                    v_ = bounce_link<I>(at_, xw + e, yw, e ? make_float2(lrec[I - 1].z, lrec[I - 1].w)         \
+                                                         : make_float2(lrec[I - 1].x, lrec[I - 1].y));       \
                 }                                                                                             \
                 if (e == 0) f_new[I].v.x = v_;                                                                \
                 else f_new[I].v.y = v_;                                                                       \
@@ -280,7 +280,7 @@ __device__ __forceinline__ float bounce_link(const At &at, int x, int y, float2 
 // moving walls (through the wall-link records).  The half-way-only instantiation keeps the
 // link code out of the kernel.
 template <class S, int NW, int RING, bool PERIODIC, class O, int GEOM = 0>
-__global__ void __launch_bounds__(32 * (NW + 1), LBM_FUSED2_MINB) k_fused2(KParams kp, int seg_rows)
+__global__ void __launch_bounds__(32 * (NW + 1), GEOM == 2 ? 3 : LBM_FUSED2_MINB) k_fused2(KParams kp, int seg_rows)
 {
     typedef FusedLayout2<S, NW, RING> L;
     constexpr int TX = L::TX, HX = L::HX, W = L::W;
@@ -463,6 +463,14 @@ __global__ void __launch_bounds__(32 * (NW + 1), LBM_FUSED2_MINB) k_fused2(KPara
                 if ((kp.solid || kp.q || kp.wall_u) && (edge || (win_m | win_0 | win_p) != 0)) {
                     const int yw = rp < 0 ? rp + ny : (rp >= ny ? rp - ny : rp);
                     const int xw = c0 < 0 ? c0 + nx : (c0 >= nx ? c0 - nx : c0);
+                    // the pair's eight link records, requested together (one 16-byte read per
+                    // direction: both nodes), so their latency is paid once
+                    float4 lrec[8];
+                    if constexpr (GEOM == 2) {
+                        const float4 *lk = reinterpret_cast<const float4 *>(kp.link + (int64_t)yw * kp.pitch + xw);
+#pragma unroll
+                        for (int d = 0; d < 8; ++d) lrec[d] = lk[(int64_t)d * (kp.plane / 2)];
+                    }
                     LBM_GEOM_LINK(1) LBM_GEOM_LINK(2) LBM_GEOM_LINK(3) LBM_GEOM_LINK(4)
                     LBM_GEOM_LINK(5) LBM_GEOM_LINK(6) LBM_GEOM_LINK(7) LBM_GEOM_LINK(8)
                 }

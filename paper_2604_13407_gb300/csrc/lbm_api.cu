@@ -276,7 +276,7 @@ static bool fused_possible(const lbm_ctx *c)
 // 16 columns wide); 512 x 4096 84 against 57.  Solid bands: 256^2 below, 512^2 19.1 against
 // 19.1 (FP16 26.5 against 21.9), 1024^2 55 against 41, 2048^2 251 against 100.  Interpolated
 // and moving walls, whose per-link work sits on the one-pass kernel's serial path: annulus
-// 1024^2 51 against 75, 2048^2 207 against 195 (FP16 258 against 211).
+// 1024^2 51 against 58, 2048^2 207 against 195 (FP16 258 against 211).
 static bool auto_prefers_fused(const lbm_ctx *c)
 {
     const int64_t n = (int64_t)c->p.nx * c->p.ny;
