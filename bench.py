@@ -197,7 +197,8 @@ def adjoint_cost(precision, nsteps, checkpoint_every=200, nx=256, ny=1024, radiu
     (nx/2, 0.88 ny), buoyant gravity g = (0, -2e-6), improved scheme.  Times nsteps forward steps and lbm_adjoint_step over
     the same nsteps (forward sweep, segment recompute and transposed steps; objective: the
     y force on the walls; buffers already allocated by a first call) with CUDA events;
-    returns the per-step times and their ratio."""
+    returns the per-step times and their ratio.  FP16 storage: per-node reference density,
+    stochastic rounding (the states of the backward sweep are stored in FP16 too)."""
     import torch
     from paper_2604_13407_gb300 import inputs as I
     from paper_2604_13407_gb300 import lbm
@@ -207,7 +208,8 @@ def adjoint_cost(precision, nsteps, checkpoint_every=200, nx=256, ny=1024, radiu
     def sim():
         p = lbm.default_params(nx=nx, ny=ny, periodic_x=0, periodic_y=1, precision=precision, scheme=1,
                                force_mode=lbm.FORCE_BUOYANT, Fx=0.0, Fy=-2e-6, T=T_07, rho_l=RHO_L,
-                               rho_g=RHO_G, rho_s=RHO_G, tau_l=0.8, tau_g=0.8)
+                               rho_g=RHO_G, rho_s=RHO_G, tau_l=0.8, tau_g=0.8, per_node_ref=1,
+                               storage_scale_log2=18 if precision == lbm.F16DEV else 0)
         s = lbm.Simulation(p, stream=torch.cuda.current_stream())
         s.init_fields(rho)
         return s
@@ -458,7 +460,7 @@ def main():
         import torch
         from paper_2604_13407_gb300 import lbm
         torch.cuda.set_device(0)
-        prec = {"f64": lbm.F64, "f32": lbm.F32}[args.precision]
+        prec = {"f64": lbm.F64, "f32": lbm.F32, "f16dev": lbm.F16DEV}[args.precision]
         print(json.dumps({"adjoint": adjoint_cost(prec, args.steps), "precision": args.precision}))
         return
 
@@ -538,7 +540,9 @@ def main():
         adjoint = {"workload": "droplet in a 256x1024 channel (radius 20, buoyant g 2e-6, walls in x, periodic y), "
                                "objective: time-averaged y force on the walls, gradient wrt (Fx, Fy, G, T)",
                    "f32": adjoint_cost(lbm.F32, 2000), "f64": adjoint_cost(lbm.F64, 400),
-                   "f32_2048": adjoint_cost(lbm.F32, 200, 50, nx=2048, ny=2048, radius=160.0)}
+                   "f16dev": adjoint_cost(lbm.F16DEV, 2000),
+                   "f32_2048": adjoint_cost(lbm.F32, 200, 50, nx=2048, ny=2048, radius=160.0),
+                   "f16dev_2048": adjoint_cost(lbm.F16DEV, 200, 50, nx=2048, ny=2048, radius=160.0)}
 
     e2e = None
     if rank == 0 and args.e2e:

@@ -242,11 +242,16 @@ LBM_API lbm_status lbm_set_param(lbm_ctx *ctx, int32_t which, double value);
  * grad and lambda0 both NULL: only the forward pass runs (the objective alone).
  * `lambda0` (may be NULL): receives dJ/d f_bar at the starting state, [9][ny][nx]
  * doubles on the host (zero at solid nodes).
- * Supported: FP64 and FP32 storage, periodic directions, resting half-way walls (domain
+ * Supported: every storage type, periodic directions, resting half-way walls (domain
  * edges and solid nodes), CONST and BUOYANT forces, one or two relaxation times;
- * LBM_ENOTSUP otherwise.  Device memory (allocated on the first call, kept until
- * lbm_destroy or a larger call): ceil(nsteps/K) + 2 (K - 1) population states, 2 K psi
- * fields and 15 planes of the arithmetic type, K = min(checkpoint_every, nsteps) (the
+ * LBM_ENOTSUP otherwise.  16-bit storage: the states are stored and recomputed as the
+ * forward steps store them (the same stochastic rounding), and the transposed step runs in
+ * FP32 on the decoded states, taking the storage's rounding as the identity (the gradient
+ * of the unrounded step along the 16-bit run's trajectory).  Device memory (allocated on
+ * the first call, kept until lbm_destroy or a larger call): ceil(nsteps/K) + 2 (K - 1)
+ * population states (with their reference-density plane), 2 K psi fields and 15 planes of
+ * the arithmetic type (FP64 for FP64 storage, FP32 otherwise), K = min(checkpoint_every,
+ * nsteps) (the
  * recompute of a segment overlaps, on a second stream, the transposed steps of the segment
  * after it); LBM_ENOMEM when it does not fit (lower checkpoint_every).  LBM_EINVAL: nsteps or
  * checkpoint_every < 1, unknown objective. */

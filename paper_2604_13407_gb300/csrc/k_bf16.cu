@@ -1,4 +1,5 @@
 // Kernel instantiations for __nv_bfloat16 population storage.
+#include "k_adjoint.cuh"
 #include "k_fused.cuh"
 #include "k_fused2.cuh"
 #include "k_twopass.cuh"
@@ -41,6 +42,12 @@ Launchers launchers_bf16()
     L.diag = &TwoPass<__nv_bfloat16>::diag;
     L.get_state = &TwoPass<__nv_bfloat16>::get_state;
     L.set_state = &TwoPass<__nv_bfloat16>::set_state;
+    L.adj_pass1 = &Adjoint<__nv_bfloat16>::pass1;
+    L.adj_pass2 = &Adjoint<__nv_bfloat16>::pass2;
+    L.adj_lambda = &Adjoint<__nv_bfloat16>::lambda;
+    L.objective = &Adjoint<__nv_bfloat16>::objective;
+    L.adj_blocks = &Adjoint<__nv_bfloat16>::blocks;
+    L.adj_reduce = &Adjoint<__nv_bfloat16>::reduce;
     L.fused_align = FusedGeom<__nv_bfloat16>::HX;
     L.fused_geometry = LBM_FUSED_PAIRS;
     return L;

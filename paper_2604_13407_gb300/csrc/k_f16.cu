@@ -1,4 +1,5 @@
 // Kernel instantiations for __half population storage.
+#include "k_adjoint.cuh"
 #include "k_fused.cuh"
 #include "k_fused2.cuh"
 #include "k_twopass.cuh"
@@ -41,6 +42,12 @@ Launchers launchers_f16()
     L.diag = &TwoPass<__half>::diag;
     L.get_state = &TwoPass<__half>::get_state;
     L.set_state = &TwoPass<__half>::set_state;
+    L.adj_pass1 = &Adjoint<__half>::pass1;
+    L.adj_pass2 = &Adjoint<__half>::pass2;
+    L.adj_lambda = &Adjoint<__half>::lambda;
+    L.objective = &Adjoint<__half>::objective;
+    L.adj_blocks = &Adjoint<__half>::blocks;
+    L.adj_reduce = &Adjoint<__half>::reduce;
     L.fused_align = FusedGeom<__half>::HX;
     L.fused_geometry = LBM_FUSED_PAIRS;
     return L;

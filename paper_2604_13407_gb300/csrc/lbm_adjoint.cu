@@ -16,6 +16,12 @@
 // transposed steps of the segment after it, so segment states and psi fields come in two
 // sets.  Device memory: ceil(n/K) checkpoints, 2 (K - 1) segment states, 2 K psi fields
 // and the adjoint planes; it is kept for the next call with the same sizes.
+//
+// 16-bit storage: a stored state is its nine planes of deviations plus, with a per-node
+// reference density, that plane; the recompute repeats the forward steps' stochastic
+// rounding (same step seeds).  The transposed step runs in FP32 on the decoded states and
+// differentiates the FP32 step through the storage, whose rounding it takes as the
+// identity: the gradient of the unrounded step along the trajectory the 16-bit run takes.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -107,7 +113,7 @@ lbm_status adjoint_run(lbm_ctx *ctx, int64_t nsteps, int32_t K, int32_t objectiv
     ContextView v = view_of(ctx);
     const lbm_params &p = *v.p;
     if (!v.L->adj_pass1) {
-        msg = "the adjoint supports FP64 and FP32 storage only";
+        msg = "no transposed step for this storage type";
         return LBM_ENOTSUP;
     }
     if (v.kp->wall_u || v.kp->q || v.kp->wall_rho) {
@@ -129,8 +135,16 @@ lbm_status adjoint_run(lbm_ctx *ctx, int64_t nsteps, int32_t K, int32_t objectiv
     cudaStream_t st = v.stream;
     const int64_t nseg = (nsteps + K - 1) / K;
     const int64_t Kseg = std::min<int64_t>(K, nsteps);
-    const size_t state_bytes = (size_t)9 * v.plane * v.elem;
-    const size_t real = v.elem;  // arithmetic type = storage type for FP64 and FP32
+    // a stored state: the nine planes, then the per-node reference plane of 16-bit storage
+    const size_t pop_bytes = (size_t)9 * v.plane * v.elem;
+    const size_t ref_bytes = v.refp[0] ? (size_t)v.plane * sizeof(float) : 0;
+    const size_t ref_at = (pop_bytes + 255) / 256 * 256;
+    const size_t state_bytes = ref_bytes ? ref_at + ref_bytes : pop_bytes;
+    auto ref_of = [&](const void *state) -> float * {
+        return ref_bytes ? reinterpret_cast<float *>(const_cast<char *>(static_cast<const char *>(state)) + ref_at)
+                         : nullptr;
+    };
+    const size_t real = v.elem == 8 ? 8 : 4;  // arithmetic type: FP64 for FP64 storage, FP32 otherwise
     const size_t plane_r = (size_t)v.plane * real;
     const size_t psi_bytes = (size_t)p.nx * p.ny * real;
     const size_t part_bytes = (size_t)v.L->adj_blocks(*v.kp) * kAdjSlots * sizeof(double);
@@ -177,10 +191,15 @@ lbm_status adjoint_run(lbm_ctx *ctx, int64_t nsteps, int32_t K, int32_t objectiv
 
     // ---- forward sweep: checkpoints and the objective
     KParams kq = *v.kp;
+    const int64_t step0 = *v.steps;  // the forward sweep's step t runs as the context's step step0 + t
     for (int64_t t = 0; t < nsteps; ++t) {
-        if (backward && t % K == 0)
-            ACK(cudaMemcpyAsync(L.ckpt[t / K], v.pops[*v.cur], state_bytes, cudaMemcpyDeviceToDevice, st),
+        if (backward && t % K == 0) {
+            ACK(cudaMemcpyAsync(L.ckpt[t / K], v.pops[*v.cur], pop_bytes, cudaMemcpyDeviceToDevice, st),
                 "checkpoint copy");
+            if (ref_bytes)
+                ACK(cudaMemcpyAsync(ref_of(L.ckpt[t / K]), v.refp[*v.cur], ref_bytes, cudaMemcpyDeviceToDevice, st),
+                    "checkpoint copy");
+        }
         lbm_status s = v.run_steps(ctx, 1);
         if (s != LBM_OK) {
             msg = "forward step failed";
@@ -190,6 +209,7 @@ lbm_status adjoint_run(lbm_ctx *ctx, int64_t nsteps, int32_t K, int32_t objectiv
         // which read those states anyway; only the last state is summed here
         if (!backward || t == nsteps - 1) {
             kq.src = v.pops[*v.cur];
+            kq.ref_src = v.refp[*v.cur];
             ACK(v.L->objective(kq, objective, inv_nfluid, L.acc, st), "objective kernel");
         }
     }
@@ -223,10 +243,13 @@ lbm_status adjoint_run(lbm_ctx *ctx, int64_t nsteps, int32_t K, int32_t objectiv
         KParams kp = *v.kp;
         for (int64_t t = t0; t < t1; ++t) {
             kp.src = t == t0 ? L.ckpt[s] : L.seg[q][t - t0 - 1];
+            kp.ref_src = ref_of(kp.src);
             kp.psi = L.psi[q][t - t0];
             ACK(v.psi_pass(kp, as->side), "psi kernel");
             if (t + 1 < t1) {
                 kp.dst = L.seg[q][t - t0];
+                kp.ref_dst = ref_of(kp.dst);
+                kp.sr_seed = v.sr_seed(step0 + t);
                 ACK(v.collide_pass(kp, as->side), "collide kernel");
             }
         }
@@ -245,6 +268,7 @@ lbm_status adjoint_run(lbm_ctx *ctx, int64_t nsteps, int32_t K, int32_t objectiv
         KParams kp = *v.kp;
         for (int64_t t = t1 - 1; t >= t0; --t) {
             kp.src = t == t0 ? L.ckpt[s] : L.seg[q][t - t0 - 1];
+            kp.ref_src = ref_of(kp.src);
             kp.psi = L.psi[q][t - t0];
             aa.g_in = have_next ? L.g[gi] : nullptr;
             aa.c_in = have_next ? L.c[gi] : nullptr;

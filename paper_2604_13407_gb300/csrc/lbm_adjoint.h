@@ -23,6 +23,7 @@ struct ContextView {
     int64_t plane;
     AdjointState **adj;
     lbm_status (*run_steps)(lbm_ctx *, int64_t);
+    uint32_t (*sr_seed)(int64_t step);  // seed of the storage's stochastic rounding at a step
     void (*bind)(lbm_ctx *, int);
     cudaError_t (*psi_pass)(const KParams &, cudaStream_t);
     cudaError_t (*collide_pass)(const KParams &, cudaStream_t);

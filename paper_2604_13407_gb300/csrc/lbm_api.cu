@@ -824,6 +824,7 @@ ContextView view_of(lbm_ctx *c)
     v.plane = c->plane;
     v.adj = &c->adj;
     v.run_steps = [](lbm_ctx *cc, int64_t n) { return run_steps(cc, n); };
+    v.sr_seed = [](int64_t t) { return sr_seed_of(t); };
     v.bind = [](lbm_ctx *cc, int src) { bind_buffers(cc, src); };
     v.psi_pass = c->L.psi_pass;
     v.collide_pass = c->L.collide_pass;
