@@ -439,6 +439,9 @@ def main():
                     help="step kernel for --geometry-only")
     ap.add_argument("--adjoint-only", type=int, default=0,
                     help="time only the adjoint against the forward step (one JSON line; for profiling)")
+    ap.add_argument("--adjoint-lattice", type=int, default=0,
+                    help="with --adjoint-only: an N x N lattice (droplet radius 160 N/2048, checkpoint every 50) "
+                         "instead of the 256 x 1024 channel")
     ap.add_argument("--oracle-sample", default=None, choices=sorted(ORACLE_SAMPLES),
                     help="(internal) time one CPU-baseline sample of the oracle and print it")
     args = ap.parse_args()
@@ -461,7 +464,10 @@ def main():
         from paper_2604_13407_gb300 import lbm
         torch.cuda.set_device(0)
         prec = {"f64": lbm.F64, "f32": lbm.F32, "f16dev": lbm.F16DEV}[args.precision]
-        print(json.dumps({"adjoint": adjoint_cost(prec, args.steps), "precision": args.precision}))
+        N = args.adjoint_lattice
+        cost = (adjoint_cost(prec, args.steps, 50, nx=N, ny=N, radius=160.0 * N / 2048.0) if N
+                else adjoint_cost(prec, args.steps))
+        print(json.dumps({"adjoint": cost, "precision": args.precision}))
         return
 
     import torch

@@ -1,5 +1,5 @@
 // Transposed (adjoint) step of the D2Q9 pseudopotential MRT update, for one storage type
-// S with arithmetic type R = S (FP64 and FP32 storage).
+// S with arithmetic type R (FP64 for FP64 storage, FP32 for FP32 and 16-bit storage).
 //
 // The step maps the stored populations A_t to A_{t+1} = Step(A_t; Fx, Fy, G, T) (Sec. 2:
 // pull streaming, moments, psi(rho) from the EOS, F_int = -G psi S with
@@ -22,8 +22,8 @@
 // quantities from A_t and the psi field of A_t, and run the chain rule back to g(x),
 // dJ/dS(x), the local part of dJ/dpsi(x) (through F_int = -G psi S) and rho(x).
 // Pass 2 (k_adj2): dJ/dpsi(x) = local part + sum_i w_i e_i . dJ/dS(x - e_i) over fluid
-// x - e_i, then c(x) = psi'(rho) dJ/dpsi.  Parameter derivatives are summed per block in
-// FP64 (warp shuffles) and added to four FP64 accumulators with one atomic per block.
+// x - e_i, then c(x) = psi'(rho) dJ/dpsi.  Parameter derivatives are summed per block
+// (warp shuffles) into per-block FP64 slots that one reduction sums at the end of the call.
 #pragma once
 
 #include "k_twopass.cuh"

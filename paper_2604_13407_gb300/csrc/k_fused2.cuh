@@ -508,6 +508,10 @@ __global__ void __launch_bounds__(32 * (NW + 1), GEOM == 2 ? 3 : LBM_FUSED2_MINB
         const float a0 = __shfl_up_sync(0xffffffffu, psi_m1.v.y, 1), b0 = __shfl_down_sync(0xffffffffu, psi_m1.v.x, 1);
         const float ap = __shfl_up_sync(0xffffffffu, psi_new.v.y, 1), bp = __shfl_down_sync(0xffffffffu, psi_new.v.x, 1);
         const int y = rp - 1;
+        // psi of the state read, for a caller that keeps it (the adjoint's recompute): the
+        // pair's own row, solid nodes included, as the psi pass writes it
+        if (kp.psi_out != nullptr && y >= yb && collides)
+            Pair2<float>::store(kp.psi_out + (int64_t)y * nx + c0, psi_m1);
         if (y >= yb && collides && (!GEOM || own_old != 3)) {
             {
                 v2 fb[9];

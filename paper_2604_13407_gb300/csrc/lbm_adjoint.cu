@@ -10,9 +10,10 @@
 // K steps (a checkpoint); <W, A_n> is summed in FP64 there, <W, A_t> of the other states by
 // the transposed passes (objective alone: every state in the forward sweep).  Backward sweep, one segment of K
 // steps at a time from the last: the states of the segment are recomputed from its
-// checkpoint with the two-pass step (whose psi pass leaves the psi field of each state in
-// a buffer of its own), then the transposed step runs from the last state of the segment
-// to the first.  The recompute of a segment runs on a second stream, overlapping the
+// checkpoint with the step kernels the context uses, each leaving the psi field of the
+// state it reads in a buffer of its own (the two-pass step's psi pass writes it anyway; the
+// one-pass step writes it on request), then the transposed step runs from the last state
+// of the segment to the first.  The recompute of a segment runs on a second stream, overlapping the
 // transposed steps of the segment after it, so segment states and psi fields come in two
 // sets.  Device memory: ceil(n/K) checkpoints, 2 (K - 1) segment states, 2 K psi fields
 // and the adjoint planes; it is kept for the next call with the same sizes.
@@ -245,12 +246,20 @@ lbm_status adjoint_run(lbm_ctx *ctx, int64_t nsteps, int32_t K, int32_t objectiv
             kp.src = t == t0 ? L.ckpt[s] : L.seg[q][t - t0 - 1];
             kp.ref_src = ref_of(kp.src);
             kp.psi = L.psi[q][t - t0];
-            ACK(v.psi_pass(kp, as->side), "psi kernel");
             if (t + 1 < t1) {
                 kp.dst = L.seg[q][t - t0];
                 kp.ref_dst = ref_of(kp.dst);
                 kp.sr_seed = v.sr_seed(step0 + t);
-                ACK(v.collide_pass(kp, as->side), "collide kernel");
+                if (v.fused_pass) {
+                    kp.psi_out = static_cast<float *>(kp.psi);
+                    ACK(v.fused_pass(kp, as->side), "fused step kernel");
+                    kp.psi_out = nullptr;
+                } else {
+                    ACK(v.psi_pass(kp, as->side), "psi kernel");
+                    ACK(v.collide_pass(kp, as->side), "collide kernel");
+                }
+            } else {
+                ACK(v.psi_pass(kp, as->side), "psi kernel");
             }
         }
         ACK(cudaEventRecord(as->recomputed[q], as->side), "event record");

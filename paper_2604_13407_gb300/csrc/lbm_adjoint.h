@@ -27,6 +27,9 @@ struct ContextView {
     void (*bind)(lbm_ctx *, int);
     cudaError_t (*psi_pass)(const KParams &, cudaStream_t);
     cudaError_t (*collide_pass)(const KParams &, cudaStream_t);
+    // the one-pass step when the context steps with it and it can write the psi field of the
+    // state it reads (FP32 arithmetic); null otherwise
+    cudaError_t (*fused_pass)(const KParams &, cudaStream_t);
     const Launchers *L;
     lbm_status (*check_error)(lbm_ctx *, std::string &msg);  // device error word of the steps
     int64_t n_fluid;

@@ -828,6 +828,7 @@ ContextView view_of(lbm_ctx *c)
     v.bind = [](lbm_ctx *cc, int src) { bind_buffers(cc, src); };
     v.psi_pass = c->L.psi_pass;
     v.collide_pass = c->L.collide_pass;
+    v.fused_pass = (c->fused_ok && c->p.precision != LBM_F64) ? c->L.fused_pass : nullptr;
     v.L = &c->L;
     v.check_error = [](lbm_ctx *cc, std::string &m) {
         lbm_status s = sync_and_check(cc, "adjoint");

@@ -67,6 +67,8 @@ struct KParams {
     const float *ref_src;  // per-node reference density planes (FP16/BF16 with per_node_ref)
     float *ref_dst;
     void *psi;             // psi field [ny*nx] in the kernel's arithmetic type
+    float *psi_out;        // one-pass kernel (FP32 arithmetic): also write psi of the state read
+                           // here ([ny*nx], as the psi pass does), or null
     const uint8_t *solid;  // [ny*nx] or null
     const double *wall_u;  // [2][ny*nx] or null
     const double *q;       // [8][ny*nx] or null

@@ -83,6 +83,67 @@ def test_fp32_adjoint_matches_reference(references, case, obj):
     assert np.abs(lam - lam_ref).max() <= 1e-5 * np.abs(lam_ref).max()
 
 
+def wide_droplet_case(nx=256, ny=40):
+    """A droplet between walls at y = -1/2 and ny - 1/2, periodic in x, wide enough for the
+    one-pass step kernel."""
+    T, rg, rl = cs_case()
+    p = cs_params(nx=nx, ny=ny, periodic_x=True, periodic_y=False, Fx=2e-6, Fy=-1e-6, scheme=1, tau_l=0.9,
+                  tau_g=0.7)
+    return p, I.droplet(nx, ny, rl, rg, 8.0, 0.4 * nx, 0.48 * ny, periodic_x=True, periodic_y=False)
+
+
+@pytest.mark.parametrize("obj", sorted(OBJ))
+def test_one_pass_recompute_matches_reference(obj):
+    """A context that steps with the one-pass kernel recomputes each segment with it (the
+    kernel also writing the psi field of the state it reads); one that steps with the
+    two-pass kernels recomputes with those.  Both against the FP64 reference adjoint, at the
+    FP32 tolerances."""
+    p, rho = wide_droplet_case()
+    A0 = initial_state(p, rho, None)
+    J_ref, g_ref, lam_ref = AR.objective_and_grad(p, A0, 12, obj, None)
+    scale = np.abs(g_ref[list(PARAM_INDEX)]).max()
+    for kernel in (lbm.KERNEL_FUSED, lbm.KERNEL_TWO_PASS):
+        sim = gpu_sim(p, None, lbm.F32, A0, kernel=kernel)
+        assert sim.kernel_in_use == kernel
+        J, g, lam = sim.adjoint(12, 5, OBJ[obj], want_lambda0=True)
+        print("kernel %d: max |dg| / scale %.2e, lambda_0 %.2e" %
+              (kernel, np.abs(g - g_ref)[list(PARAM_INDEX)].max() / scale,
+               np.abs(lam - lam_ref).max() / np.abs(lam_ref).max()))
+        assert abs(J - J_ref) <= 1e-4 * abs(J_ref) + 1e-8
+        for k in PARAM_INDEX:
+            assert abs(g[k] - g_ref[k]) <= 1e-5 * scale, (kernel, k, g[k], g_ref[k])
+        assert np.abs(lam - lam_ref).max() <= 1e-5 * np.abs(lam_ref).max()
+
+
+@pytest.mark.parametrize("obj", sorted(OBJ))
+def test_replicated_lattice_adds_up(obj):
+    """Four copies of a 512 x 1024 state side by side (2048 x 1024, periodic in x) evolve as
+    four copies, so the mean x momentum and its gradient equal the single copy's and
+    lambda_0 is a quarter of it per copy; the wall force, its gradient and lambda_0 add up
+    over the copies (J four times the copy's, lambda_0 the copy's).  Both lattices step and
+    recompute with the one-pass kernel; the larger one has four times the blocks, strips and
+    per-block partial sums."""
+    p1, rho = wide_droplet_case(512, 1024)
+    p4, _ = wide_droplet_case(2048, 1024)
+    small = lbm.Simulation(GC.gpu_params(p1, lbm.F32))
+    small.init_fields(rho)
+    A = small.get_state()
+    small.set_state(A)
+    big = lbm.Simulation(GC.gpu_params(p4, lbm.F32))
+    big.set_state(np.tile(A, (1, 1, 4)))
+    J1, g1, lam1 = small.adjoint(12, 5, OBJ[obj], want_lambda0=True)
+    J4, g4, lam4 = big.adjoint(12, 5, OBJ[obj], want_lambda0=True)
+    k = 1.0 if obj == "mean_jx" else 4.0
+    scale = np.abs(g1[list(PARAM_INDEX)]).max()
+    print("J %.9e / %.9e; max |dg| / scale %.2e" % (J1, J4 / k, np.abs(g4 / k - g1).max() / scale))
+    assert abs(J4 / k - J1) <= 1e-6 * abs(J1)
+    for q in PARAM_INDEX:
+        assert abs(g4[q] / k - g1[q]) <= 1e-6 * scale, (q, g4[q], g1[q])
+    lam_copy = lam4.reshape(9, 1024, 4, 512) * (4.0 if obj == "mean_jx" else 1.0)
+    for c in range(4):
+        assert np.abs(lam_copy[:, :, c, :] - lam1).max() <= 1e-6 * np.abs(lam1).max()
+
+
 def test_checkpoint_interval_does_not_change_the_result(references):
     p, solid, A0, *_ = references[("droplet_case", "wall_force_y")]
     res = []
