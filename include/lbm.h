@@ -119,6 +119,12 @@ typedef struct lbm_params {
                                        momentum; stochastic rounding leaves a zero-mean error
                                        (but no longer keeps mirror-symmetric states exactly
                                        symmetric).  The initial state is rounded to nearest. */
+    int32_t diag_every;             /* 0 (default): lbm_step never waits for the device.  D > 0:
+                                       whenever the step count reaches a multiple of D, lbm_step
+                                       waits, evaluates the diagnostics and returns LBM_ENAN (a
+                                       non-finite density or velocity) or the status of the
+                                       device error word; the steps after that point are not
+                                       run.  The adjoint's forward sweep does not check. */
     double a, b, R, T, K_eos;       /* EOS coefficients */
     double G;                       /* interaction strength, < 0 (Sec. 2) */
     double k1, k2;                  /* source coefficients, epsilon = -8 (k1 + k2) */
@@ -197,11 +203,13 @@ LBM_API lbm_status lbm_init_fields(lbm_ctx *ctx, const double *rho, const double
                            int on_device);
 
 /* Advance nsteps time steps on the context stream.  Launches the kernels and returns
- * without waiting for the device.  A device-side failure of a launched step (a bounded
- * wait that ran out: LBM_ETIMEOUT; a bounds check: LBM_EBOUNDS) is recorded in a device
- * error word and reported by the next call that waits for the stream: lbm_sync,
- * lbm_get_moments / lbm_get_state with host buffers, lbm_get_diagnostics, lbm_save_state
- * and lbm_adjoint_step. */
+ * without waiting for the device, unless lbm_params.diag_every = D > 0: then it waits at
+ * every step count that is a multiple of D, and stops there with LBM_ENAN (non-finite
+ * density or velocity) or the device error status.  A device-side failure of a launched
+ * step (a bounded wait that ran out: LBM_ETIMEOUT; a bounds check: LBM_EBOUNDS) is
+ * recorded in a device error word and reported by the next call that waits for the
+ * stream: lbm_sync, lbm_get_moments / lbm_get_state with host buffers,
+ * lbm_get_diagnostics, lbm_save_state, lbm_adjoint_step and the diag_every checks. */
 LBM_API lbm_status lbm_step(lbm_ctx *ctx, int64_t nsteps);
 
 /* Density and velocity of the current state (the state the next step pulls), computed

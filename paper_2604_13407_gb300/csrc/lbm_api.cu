@@ -131,6 +131,7 @@ static lbm_status validate(lbm_ctx *c, const lbm_params &p)
     if (p.tau_l != p.tau_g && !(p.rho_l > p.rho_g)) return fail(c, LBM_EINVAL, "rho_l must exceed rho_g when tau_l != tau_g");
     if (p.storage_scale_log2 < -30 || p.storage_scale_log2 > 30) return fail(c, LBM_EINVAL, "storage_scale_log2 out of range");
     if (p.storage_rounding != 0 && p.storage_rounding != 1) return fail(c, LBM_EINVAL, "storage_rounding must be 0 or 1");
+    if (p.diag_every < 0) return fail(c, LBM_EINVAL, "diag_every must be >= 0");
     if (p.precision == LBM_F16DEV && (p.storage_scale_log2 < -15 || p.storage_scale_log2 > 24))
         return fail(c, LBM_EINVAL, "FP16 storage needs storage_scale_log2 in [-15, 24] (2^-k must be an FP16 value)");
     double rmax = p.rho_max > 0 ? p.rho_max : 1.25 * std::fmax(std::fmax(p.rho_l, p.rho_g), p.rho_s);
@@ -607,7 +608,20 @@ extern "C" lbm_status lbm_step(lbm_ctx *c, int64_t nsteps)
     if (!c) return LBM_EINVAL;
     if (!c->initialised) return fail(c, LBM_ESTATE, "fields not initialised");
     if (nsteps < 0) return fail(c, LBM_EINVAL, "nsteps < 0");
-    return run_steps(c, nsteps);
+    const int64_t D = c->p.diag_every;
+    if (D <= 0) return run_steps(c, nsteps);
+    // launch up to the next multiple of D, then wait and check the state there
+    while (nsteps > 0) {
+        const int64_t n = std::min<int64_t>(nsteps, D - c->steps % D);
+        lbm_status s = run_steps(c, n);
+        if (s != LBM_OK) return s;
+        nsteps -= n;
+        if (c->steps % D == 0) {
+            double d[LBM_NDIAG];
+            if ((s = lbm_get_diagnostics(c, d)) != LBM_OK) return s;
+        }
+    }
+    return LBM_OK;
 }
 
 // psi field of the current state (needed by the moments and diagnostics kernels)

@@ -39,7 +39,7 @@ class LbmParams(ctypes.Structure):
         ("q2_original", ctypes.c_int32), ("eos", ctypes.c_int32),
         ("force_mode", ctypes.c_int32), ("kernel", ctypes.c_int32),
         ("per_node_ref", ctypes.c_int32), ("storage_scale_log2", ctypes.c_int32),
-        ("storage_rounding", ctypes.c_int32),
+        ("storage_rounding", ctypes.c_int32), ("diag_every", ctypes.c_int32),
         ("a", ctypes.c_double), ("b", ctypes.c_double), ("R", ctypes.c_double),
         ("T", ctypes.c_double), ("K_eos", ctypes.c_double),
         ("G", ctypes.c_double), ("k1", ctypes.c_double), ("k2", ctypes.c_double),

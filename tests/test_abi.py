@@ -38,10 +38,12 @@ def test_struct_layout_matches():
     assert p.struct_size == ctypes.sizeof(lbm.LbmParams)
     assert p.nx == 4 and p.ny == 128 and p.precision == lbm.F64
     assert p.k1 == pytest.approx(-1.895 / 16)
+    assert p.diag_every == 0 and p.storage_rounding == 1
 
 
 @pytest.mark.parametrize("field,value", [("nx", 0), ("ny", 65536), ("tau_l", 0.5), ("G", 0.5), ("Lambda", 0.0),
-                                         ("precision", 7), ("eos", 3), ("kernel", 9), ("storage_rounding", 2)])
+                                         ("precision", 7), ("eos", 3), ("kernel", 9), ("storage_rounding", 2),
+                                         ("diag_every", -1)])
 def test_create_rejects_invalid_parameters(field, value):
     p = lbm.default_params(**{field: value})
     with pytest.raises(lbm.LbmError) as e:

@@ -13,8 +13,10 @@ import numpy as np
 import pytest
 
 from oracle import oracle as O
+from paper_2604_13407_gb300 import inputs as I
 from paper_2604_13407_gb300 import lbm
 from tests import gpu_cases as GC
+from tests.setups import cs_case, cs_params
 
 pytestmark = pytest.mark.gpu
 
@@ -239,3 +241,32 @@ def test_nan_is_reported():
     with pytest.raises(lbm.LbmError) as e:
         sim.diagnostics()
     assert e.value.status == 5
+
+
+@pytest.mark.parametrize("kernel", [lbm.KERNEL_TWO_PASS, lbm.KERNEL_FUSED])
+def test_diag_every_stops_at_the_first_check(kernel):
+    """diag_every = 10: lbm_step waits at step counts 10, 20, ...; a state that turns
+    non-finite stops the call at the first such count with LBM_ENAN.  A healthy state runs
+    through every check; diag_every = 0 never checks."""
+    n = 256
+    T, rg, rl = cs_case()
+    p0 = cs_params(nx=n, ny=48, periodic_x=True, periodic_y=False, scheme=1)
+    rho0 = I.droplet(n, 48, rl, rg, 10.0, 100.3, 23.6, periodic_x=True, periodic_y=False)
+    for every in (10, 0):
+        sim = lbm.Simulation(GC.gpu_params(p0, lbm.F32, kernel, diag_every=every))
+        assert sim.kernel_in_use == kernel
+        sim.init_fields(rho0)
+        sim.step(35)
+        assert sim.step_count == 35
+        sim.step(3)
+        A = sim.get_state()
+        A[3, 20, 7] = np.nan
+        sim.set_state(A)  # resets the step count
+        if every:
+            with pytest.raises(lbm.LbmError) as e:
+                sim.step(100)
+            assert e.value.status == 5 and sim.step_count == 10
+        else:
+            sim.step(100)
+            assert sim.step_count == 100
+        sim.close()
