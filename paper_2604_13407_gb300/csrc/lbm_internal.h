@@ -137,7 +137,7 @@ struct Launchers {
                         cudaStream_t);
     cudaError_t (*get_state)(const KParams &, double *out, cudaStream_t);
     cudaError_t (*set_state)(const KParams &, const double *in, cudaStream_t);
-    // transposed step (FP32 arithmetic for FP32 and 16-bit storage); AdjArgs in k_adjoint.cuh
+    // transposed step (FP64 arithmetic for FP64 storage, FP32 otherwise); AdjArgs in k_adjoint.cuh
     cudaError_t (*adj_pass1)(const KParams &, const AdjArgs &, cudaStream_t);
     cudaError_t (*adj_pass2)(const KParams &, const AdjArgs &, cudaStream_t);
     cudaError_t (*adj_lambda)(const KParams &, const AdjArgs &, double *out, cudaStream_t);
