@@ -117,14 +117,11 @@ __device__ __forceinline__ void p_eos_derivs(const KParams &kp, R rho, R &p_rho,
 // call and reduced once at its end, so no atomic is contended and the summation order is
 // fixed.
 
-// Warp sum of one value per lane, returned as a double.  FP64 arithmetic sums in FP64;
-// FP32 arithmetic sums compensated pairs (Knuth's TwoSum at every shuffle level, about
-// 2^-48 relative) and converts once, which keeps FP64 work (a narrow pipe on GB300) out of
-// the per-node path.
-__device__ __forceinline__ double warp_sum_r(double v) { return warp_sum(v); }
-__device__ __forceinline__ double warp_sum_r(float v)
+// Warp sum of one value per lane as a compensated FP32 pair (hi, lo) in lane 0: Knuth's
+// TwoSum at every shuffle level, about 2^-48 relative.
+__device__ __forceinline__ void warp_sum_pair(float &hi, float &lo)
 {
-    float hi = v, lo = 0.f;
+    lo = 0.f;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
         const float ohi = __shfl_down_sync(0xffffffffu, hi, o), olo = __shfl_down_sync(0xffffffffu, lo, o);
@@ -132,29 +129,45 @@ __device__ __forceinline__ double warp_sum_r(float v)
         lo += olo + ((hi - (sum - z)) + (ohi - z));
         hi = sum;
     }
-    return double(hi) + double(lo);
 }
 
-// Block sum of N per-thread values added to this block's slots [first, first + N).
+// Block sum of N per-thread values added to this block's slots [first, first + N).  FP64
+// arithmetic sums in FP64.  FP32 arithmetic keeps each warp's sum as a compensated FP32 pair
+// and converts to FP64 only in the block's final step (N threads), which keeps FP64 work
+// (a narrow pipe on GB300) out of the per-node path.
 template <int N, class R>
 __device__ __forceinline__ void block_add(const R (&v)[N], double *part, int first)
 {
-    __shared__ double red[kRowThreads / 32][N];
-    double w[N];
-    // a quantity that is zero on every lane of the warp (the wall terms away from walls) sums
-    // to exactly zero: skip its shuffles
-#pragma unroll
-    for (int k = 0; k < N; ++k) w[k] = __any_sync(0xffffffffu, v[k] != R(0)) ? warp_sum_r(v[k]) : 0.0;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    if (lane == 0)
+    double t = 0.0;
+    if constexpr (sizeof(R) == 8) {
+        __shared__ double red[kRowThreads / 32][N];
+        // a quantity that is zero on every lane of the warp (the wall terms away from walls)
+        // sums to exactly zero: skip its shuffles
 #pragma unroll
-        for (int k = 0; k < N; ++k) red[wid][k] = w[k];
-    __syncthreads();
-    if (threadIdx.x < N) {
-        double t = 0.0;
-        for (int q = 0; q < kRowThreads / 32; ++q) t += red[q][threadIdx.x];
-        part[((int64_t)blockIdx.y * gridDim.x + blockIdx.x) * kAdjSlots + first + threadIdx.x] += t;
+        for (int k = 0; k < N; ++k) {
+            const double w = __any_sync(0xffffffffu, v[k] != R(0)) ? warp_sum(double(v[k])) : 0.0;
+            if (lane == 0) red[wid][k] = w;
+        }
+        __syncthreads();
+        if (threadIdx.x < N)
+            for (int q = 0; q < kRowThreads / 32; ++q) t += red[q][threadIdx.x];
+    } else {
+        __shared__ float2 red[kRowThreads / 32][N];
+#pragma unroll
+        for (int k = 0; k < N; ++k) {
+            float hi = float(v[k]), lo = 0.f;
+            if (__any_sync(0xffffffffu, v[k] != R(0))) warp_sum_pair(hi, lo);
+            if (lane == 0) red[wid][k] = make_float2(hi, lo);
+        }
+        __syncthreads();
+        if (threadIdx.x < N)
+            for (int q = 0; q < kRowThreads / 32; ++q) {
+                const float2 p = red[q][threadIdx.x];
+                t += double(p.x) + double(p.y);
+            }
     }
+    if (threadIdx.x < N) part[((int64_t)blockIdx.y * gridDim.x + blockIdx.x) * kAdjSlots + first + threadIdx.x] += t;
 }
 
 // Block sum of one double added to *acc with one FP64 atomic per block.
@@ -182,12 +195,12 @@ __global__ void __launch_bounds__(kRowThreads) k_adj1(KParams kp, AdjArgs aa)
     const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y;
     const int64_t node = (int64_t)y * kp.nx + x, k = (int64_t)y * kp.pitch + x;
     R gFx = R(0), gFy = R(0), gG = R(0), gT = R(0), Jt = R(0);
-    const R inv_nf = R(aa.inv_nfluid);
+    const R inv_nf = sizeof(R) == 8 ? R(aa.inv_nfluid) : R(aa.inv_nfluid_f);
     if (x < kp.nx && !node_is_solid(kp, node)) {
         const Consts<R> &cc = cst<R>(kp);
         const unsigned wm = wall_mask(kp, x, y);
         R lam[9];
-        lambda_at<R>(kp, aa, x, y, wm, R(aa.w_scale), inv_nf, lam);
+        lambda_at<R>(kp, aa, x, y, wm, sizeof(R) == 8 ? R(aa.w_scale) : R(aa.w_scale_f), inv_nf, lam);
 
         // ---- forward quantities at this node: the pull of Eq. (lbe.str) with half-way walls
         // (the only walls the adjoint accepts): f_i = A_o(x) + 0 when x - e_i is a wall, as

@@ -226,8 +226,10 @@ lbm_status adjoint_run(lbm_ctx *ctx, int64_t nsteps, int32_t K, int32_t objectiv
     // ---- backward sweep
     AdjArgs aa{};
     aa.w_scale = w;
+    aa.w_scale_f = float(w);
     aa.objective = objective;
     aa.inv_nfluid = inv_nfluid;
+    aa.inv_nfluid_f = float(inv_nfluid);
     aa.part = L.part;
     aa.dS = L.dS;
     aa.dpsi = L.dpsi;

@@ -107,6 +107,8 @@ struct AdjArgs {
     double inv_nfluid;  // 1 / number of fluid nodes (objective 1)
     double *part;       // per-block FP64 partial sums [blocks][kAdjSlots]
     int sum_J;          // pass 1 also sums <W, A_t> of its state
+    float w_scale_f, inv_nfluid_f;  // the two scales rounded to FP32 on the host (FP32 arithmetic
+                                    // converts no FP64 value per node)
 };
 
 // Storage precisions (match lbm_precision)
