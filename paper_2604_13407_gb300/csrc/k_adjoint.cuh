@@ -39,28 +39,70 @@ __device__ __forceinline__ bool wall_link(const KParams &kp, int x, int y, int i
     return false;
 }
 
-// Walls among the eight neighbours of (x, y): bit i set when x + e_i is a solid node or lies
-// beyond a non-periodic edge.  One set of global solid-flag reads per node serves the pull
+// The 3 x 3 neighbourhood of node (x, y), computed once per node so that the wall mask,
+// lambda_{t+1}, the pull, the psi stencil and the dJ/dS gather share one set of index
+// arithmetic: the columns x - 1, x, x + 1 and rows y - 1, y, y + 1 wrapped along periodic
+// directions, and bit i set when x + e_i lies inside the lattice.  A neighbour beyond a
+// non-periodic edge takes the node's own column or row, so no index leaves the lattice even
+// where it is not used.  k(i): pitched plane index of x + e_i; n(i): its psi-field index
+// (nx * ny < 2^31).
+struct Around {
+    const KParams &kp;
+    int xc[3], yr[3];
+    unsigned inside;
+    __device__ __forceinline__ int64_t k(int i) const { return (int64_t)yr[ey_(i) + 1] * kp.pitch + xc[ex_(i) + 1]; }
+    __device__ __forceinline__ int64_t n(int i) const { return (int64_t)(yr[ey_(i) + 1] * kp.nx + xc[ex_(i) + 1]); }
+    __device__ __forceinline__ bool in(int i) const { return (inside >> i) & 1u; }
+};
+
+__device__ __forceinline__ Around around(const KParams &kp, int x, int y)
+{
+    Around a{kp};
+    bool okx[3], oky[3];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        int xx = x + d - 1, yy = y + d - 1;
+        okx[d] = oky[d] = true;
+        if (xx < 0 || xx >= kp.nx) {
+            if (kp.periodic_x) xx = xx < 0 ? xx + kp.nx : xx - kp.nx;
+            else okx[d] = false, xx = x;
+        }
+        if (yy < 0 || yy >= kp.ny) {
+            if (kp.periodic_y) yy = yy < 0 ? yy + kp.ny : yy - kp.ny;
+            else oky[d] = false, yy = y;
+        }
+        a.xc[d] = xx;
+        a.yr[d] = yy;
+    }
+    a.inside = 0;
+#pragma unroll
+    for (int i = 0; i < 9; ++i)
+        if (okx[ex_(i) + 1] && oky[ey_(i) + 1]) a.inside |= 1u << i;
+    return a;
+}
+
+// Walls among the eight neighbours: bit i set when x + e_i is a solid node or lies beyond a
+// non-periodic edge.  One set of global solid-flag reads per node serves the pull
 // (population i comes from x - e_i = x + e_opp(i)), lambda_{t+1}, the objective and the wall
 // psi terms.
-__device__ __forceinline__ unsigned wall_mask(const KParams &kp, int x, int y)
+__device__ __forceinline__ unsigned wall_mask(const KParams &kp, const Around &nb)
 {
     unsigned wm = 0;
 #pragma unroll
-    for (int i = 1; i < 9; ++i) {
-        int64_t kn;
-        if (wall_link(kp, x, y, i, kn)) wm |= 1u << i;
-    }
+    for (int i = 1; i < 9; ++i)
+        if (!nb.in(i) || (kp.solid != nullptr && kp.solid[nb.n(i)] != 0)) wm |= 1u << i;
     return wm;
 }
 
-// Row-major pitched index of the fluid neighbour x + e_i (wrapped along periodic directions).
-__device__ __forceinline__ int64_t neighbour_k(const KParams &kp, int x, int y, int i)
-{
-    int xn = x + ex_(i), yn = y + ey_(i);
-    wrap_xy(kp, xn, yn);
-    return (int64_t)yn * kp.pitch + xn;
-}
+// psi at the eight neighbours for the stencil S: the psi field inside the lattice (solid
+// nodes hold psi of their virtual density there), psi(rho_s) beyond a non-periodic edge.
+template <class R>
+struct AroundPsi {
+    const KParams &kp;
+    const R *psi;
+    const Around &nb;
+    __device__ __forceinline__ R operator()(int i) const { return nb.in(i) ? psi[nb.n(i)] : cst<R>(kp).psi_s; }
+};
 
 // Objective weights W_i(x) at a fluid node (before the 1/n of the time average);
 // inv_nf = 1 / number of fluid nodes in the arithmetic type.
@@ -71,18 +113,19 @@ __device__ __forceinline__ R objective_weight(int objective, int i, bool wall_ah
     return R(ex_(i)) * inv_nf;
 }
 
-// lambda_{t+1} of the nine populations of fluid node (x, y); wm its wall_mask.
+// lambda_{t+1} of the nine populations of a fluid node: nb its neighbourhood, wm its
+// wall_mask.
 template <class R>
-__device__ __forceinline__ void lambda_at(const KParams &kp, const AdjArgs &aa, int x, int y, unsigned wm, R wscale,
+__device__ __forceinline__ void lambda_at(const KParams &kp, const AdjArgs &aa, const Around &nb, unsigned wm, R wscale,
                                           R inv_nf, R (&lam)[9])
 {
-    const int64_t k = (int64_t)y * kp.pitch + x;
+    const int64_t k = nb.k(0);
     const R *g = static_cast<const R *>(aa.g_in);
     const R *c = static_cast<const R *>(aa.c_in);
 #pragma unroll
     for (int i = 0; i < 9; ++i) {
         const bool wall = (i != 0) && ((wm >> i) & 1u);
-        const int64_t kn = (i == 0 || wall) ? k : neighbour_k(kp, x, y, i);
+        const int64_t kn = (i == 0 || wall) ? k : nb.k(i);
         R v = wscale * objective_weight<R>(aa.objective, i, wall, inv_nf);
         if (g != nullptr) {
             if (wall) v += g[opp_(i) * kp.plane + k] + c[k];
@@ -187,7 +230,7 @@ __device__ __forceinline__ void block_atomic_add(double v, double *acc)
 
 // Pass 1 of the transposed step at A_t (kp.src) with the psi field of A_t (kp.psi).
 template <class S>
-__global__ void __launch_bounds__(kRowThreads) k_adj1(KParams kp, AdjArgs aa)
+__global__ void __launch_bounds__(kRowThreads, sizeof(typename Codec<S>::R) == 8 ? 4 : 8) k_adj1(KParams kp, AdjArgs aa)
 {
     typedef typename Codec<S>::R R;
     grid_dependency_wait();
@@ -198,24 +241,20 @@ __global__ void __launch_bounds__(kRowThreads) k_adj1(KParams kp, AdjArgs aa)
     const R inv_nf = sizeof(R) == 8 ? R(aa.inv_nfluid) : R(aa.inv_nfluid_f);
     if (x < kp.nx && !node_is_solid(kp, node)) {
         const Consts<R> &cc = cst<R>(kp);
-        const unsigned wm = wall_mask(kp, x, y);
+        const Around nb = around(kp, x, y);
+        const unsigned wm = wall_mask(kp, nb);
         R lam[9];
-        lambda_at<R>(kp, aa, x, y, wm, sizeof(R) == 8 ? R(aa.w_scale) : R(aa.w_scale_f), inv_nf, lam);
+        lambda_at<R>(kp, aa, nb, wm, sizeof(R) == 8 ? R(aa.w_scale) : R(aa.w_scale_f), inv_nf, lam);
 
         // ---- forward quantities at this node: the pull of Eq. (lbe.str) with half-way walls
         // (the only walls the adjoint accepts): f_i = A_o(x) + 0 when x - e_i is a wall, as
         // the forward step's bounce-back rule evaluates it
         R f[9];
-        f[0] = load_pop<S>(kp, 0, x, y);
+        f[0] = load_pop_at<S>(kp, 0, k);
 #pragma unroll
         for (int i = 1; i < 9; ++i) {
-            if ((wm >> opp_(i)) & 1u) {
-                f[i] = load_pop<S>(kp, opp_(i), x, y) + R(0);
-            } else {
-                int xs = x - ex_(i), ys = y - ey_(i);
-                wrap_xy(kp, xs, ys);
-                f[i] = load_pop<S>(kp, i, xs, ys);
-            }
+            if ((wm >> opp_(i)) & 1u) f[i] = load_pop_at<S>(kp, opp_(i), k) + R(0);
+            else f[i] = load_pop_at<S>(kp, i, nb.k(opp_(i)));  // x - e_i = x + e_opp(i)
         }
         const R rho = density<R>(f);
         const R jx = ((f[1] - f[3]) + (f[5] - f[6])) + (f[8] - f[7]);
@@ -238,7 +277,7 @@ __global__ void __launch_bounds__(kRowThreads) k_adj1(KParams kp, AdjArgs aa)
         const R *psif = static_cast<const R *>(kp.psi);
         const R psi = psif[node];
         R Sx, Sy, Fex, Fey;
-        stencil_S<R>(FieldPsi<R>{kp, psif, x, y}, Sx, Sy);
+        stencil_S<R>(AroundPsi<R>{kp, psif, nb}, Sx, Sy);
         external_force<R>(kp, node, rho, Fex, Fey);
         const R G = cc.G;
         const R Fx = -G * psi * Sx + Fex, Fy = -G * psi * Sy + Fey;
@@ -399,13 +438,14 @@ __global__ void __launch_bounds__(kRowThreads) k_adj2(KParams kp, AdjArgs aa)
         const Consts<R> &cc = cst<R>(kp);
         const R *dS = static_cast<const R *>(aa.dS);
         R dpsi = static_cast<const R *>(aa.dpsi)[k];
+        const Around nb = around(kp, x, y);
 #pragma unroll
         for (int i = 1; i < 9; ++i) {
-            // the node z = x - e_i has x in its stencil along e_i
-            int xz = x - ex_(i), yz = y - ey_(i);
-            if (!wrap_xy(kp, xz, yz)) continue;
-            if (kp.solid != nullptr && kp.solid[(int64_t)yz * kp.nx + xz] != 0) continue;
-            const int64_t kz = (int64_t)yz * kp.pitch + xz;
+            // the node z = x - e_i = x + e_opp(i) has x in its stencil along e_i
+            const int o = opp_(i);
+            if (!nb.in(o)) continue;
+            if (kp.solid != nullptr && kp.solid[nb.n(o)] != 0) continue;
+            const int64_t kz = nb.k(o);
             dpsi += omega_<R>(i) * (R(ex_(i)) * dS[kz] + R(ey_(i)) * dS[kp.plane + kz]);
         }
         const R rho = static_cast<const R *>(aa.rho)[k];
@@ -435,7 +475,8 @@ __global__ void __launch_bounds__(kRowThreads) k_adj_lambda(KParams kp, AdjArgs 
 #pragma unroll
         for (int i = 0; i < 9; ++i) lam[i] = R(0);
     } else {
-        lambda_at<R>(kp, aa, x, y, wall_mask(kp, x, y), R(0), R(aa.inv_nfluid), lam);
+        const Around nb = around(kp, x, y);
+        lambda_at<R>(kp, aa, nb, wall_mask(kp, nb), R(0), R(aa.inv_nfluid), lam);
     }
 #pragma unroll
     for (int i = 0; i < 9; ++i) out[i * n + node] = double(lam[i]);

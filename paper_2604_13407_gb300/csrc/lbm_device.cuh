@@ -219,16 +219,21 @@ __device__ __forceinline__ bool is_wall_at(const KParams &kp, int x, int y)
 }
 
 // ------------------------------------------------------- global access ------
-// Population i of node (x, y) of the source state, decoded.
+// Population i of the source state at pitched index k (or at node (x, y)), decoded.
 template <class S>
-__device__ __forceinline__ typename Codec<S>::R load_pop(const KParams &kp, int i, int x, int y)
+__device__ __forceinline__ typename Codec<S>::R load_pop_at(const KParams &kp, int i, int64_t k)
 {
     typedef typename Codec<S>::R R;
     const S *A = static_cast<const S *>(kp.src);
-    const int64_t k = (int64_t)y * kp.pitch + x;
     R wref = R(0);
     if constexpr (IsDev<S>::value) wref = __fmul_rn(w_<R>(i), kp.per_node_ref ? R(kp.ref_src[k]) : cst<R>(kp).rho_ref);
     return Codec<S>::dec(A[i * kp.plane + k], wref, cst<R>(kp).inv_scale);
+}
+
+template <class S>
+__device__ __forceinline__ typename Codec<S>::R load_pop(const KParams &kp, int i, int x, int y)
+{
+    return load_pop_at<S>(kp, i, (int64_t)y * kp.pitch + x);
 }
 
 // Link closed by a wall (x - e_i is a wall): the population that left (x, y) toward it
