@@ -39,48 +39,6 @@ __device__ __forceinline__ bool wall_link(const KParams &kp, int x, int y, int i
     return false;
 }
 
-// The 3 x 3 neighbourhood of node (x, y), computed once per node so that the wall mask,
-// lambda_{t+1}, the pull, the psi stencil and the dJ/dS gather share one set of index
-// arithmetic: the columns x - 1, x, x + 1 and rows y - 1, y, y + 1 wrapped along periodic
-// directions, and bit i set when x + e_i lies inside the lattice.  A neighbour beyond a
-// non-periodic edge takes the node's own column or row, so no index leaves the lattice even
-// where it is not used.  k(i): pitched plane index of x + e_i; n(i): its psi-field index
-// (nx * ny < 2^31).
-struct Around {
-    const KParams &kp;
-    int xc[3], yr[3];
-    unsigned inside;
-    __device__ __forceinline__ int64_t k(int i) const { return (int64_t)yr[ey_(i) + 1] * kp.pitch + xc[ex_(i) + 1]; }
-    __device__ __forceinline__ int64_t n(int i) const { return (int64_t)(yr[ey_(i) + 1] * kp.nx + xc[ex_(i) + 1]); }
-    __device__ __forceinline__ bool in(int i) const { return (inside >> i) & 1u; }
-};
-
-__device__ __forceinline__ Around around(const KParams &kp, int x, int y)
-{
-    Around a{kp};
-    bool okx[3], oky[3];
-#pragma unroll
-    for (int d = 0; d < 3; ++d) {
-        int xx = x + d - 1, yy = y + d - 1;
-        okx[d] = oky[d] = true;
-        if (xx < 0 || xx >= kp.nx) {
-            if (kp.periodic_x) xx = xx < 0 ? xx + kp.nx : xx - kp.nx;
-            else okx[d] = false, xx = x;
-        }
-        if (yy < 0 || yy >= kp.ny) {
-            if (kp.periodic_y) yy = yy < 0 ? yy + kp.ny : yy - kp.ny;
-            else oky[d] = false, yy = y;
-        }
-        a.xc[d] = xx;
-        a.yr[d] = yy;
-    }
-    a.inside = 0;
-#pragma unroll
-    for (int i = 0; i < 9; ++i)
-        if (okx[ex_(i) + 1] && oky[ey_(i) + 1]) a.inside |= 1u << i;
-    return a;
-}
-
 // Walls among the eight neighbours: bit i set when x + e_i is a solid node or lies beyond a
 // non-periodic edge.  One set of global solid-flag reads per node serves the pull
 // (population i comes from x - e_i = x + e_opp(i)), lambda_{t+1}, the objective and the wall
@@ -93,16 +51,6 @@ __device__ __forceinline__ unsigned wall_mask(const KParams &kp, const Around &n
         if (!nb.in(i) || (kp.solid != nullptr && kp.solid[nb.n(i)] != 0)) wm |= 1u << i;
     return wm;
 }
-
-// psi at the eight neighbours for the stencil S: the psi field inside the lattice (solid
-// nodes hold psi of their virtual density there), psi(rho_s) beyond a non-periodic edge.
-template <class R>
-struct AroundPsi {
-    const KParams &kp;
-    const R *psi;
-    const Around &nb;
-    __device__ __forceinline__ R operator()(int i) const { return nb.in(i) ? psi[nb.n(i)] : cst<R>(kp).psi_s; }
-};
 
 // Objective weights W_i(x) at a fluid node (before the 1/n of the time average);
 // inv_nf = 1 / number of fluid nodes in the arithmetic type.

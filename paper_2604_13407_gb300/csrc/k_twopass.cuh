@@ -13,6 +13,7 @@ template <class S>
 struct GlobalAt {
     const KParams &kp;
     __device__ __forceinline__ typename Codec<S>::R operator()(int k, int x, int y) const { return load_pop<S>(kp, k, x, y); }
+    __device__ __forceinline__ typename Codec<S>::R at_k(int k, int64_t kk) const { return load_pop_at<S>(kp, k, kk); }
 };
 
 // psi of the neighbour along e_i of (x, y), read from the psi field written by the psi
@@ -29,6 +30,16 @@ struct FieldPsi {
         if (!wrap_xy(kp, xx, yy)) return cst<R>(kp).psi_s;
         return psi[(int64_t)yy * kp.nx + xx];
     }
+};
+
+// FieldPsi from the node's neighbourhood nb: the psi field inside the lattice (solid
+// nodes hold psi of their virtual density there), psi(rho_s) beyond a non-periodic edge.
+template <class R>
+struct AroundPsi {
+    const KParams &kp;
+    const R *psi;
+    const Around &nb;
+    __device__ __forceinline__ R operator()(int i) const { return nb.in(i) ? psi[nb.n(i)] : cst<R>(kp).psi_s; }
 };
 
 __device__ __forceinline__ bool node_is_solid(const KParams &kp, int64_t node)
@@ -52,7 +63,7 @@ __global__ void __launch_bounds__(kRowThreads) k_psi(KParams kp)
         return;
     }
     R f[9];
-    pull_node<R>(kp, x, y, GlobalAt<S>{kp}, f, (R *)nullptr);
+    pull_node_nb<R>(kp, around(kp, x, y), x, y, GlobalAt<S>{kp}, f, (R *)nullptr);
     psi[node] = psi_of<R>(kp, density<R>(f));
 }
 
@@ -69,9 +80,10 @@ __global__ void __launch_bounds__(kRowThreads) k_collide(KParams kp)
     if (node_is_solid(kp, node)) return;
     const R *psi = static_cast<const R *>(kp.psi);
     R f[9], fb[9], Sx, Sy, Fex, Fey, ux, uy;
-    pull_node<R>(kp, x, y, GlobalAt<S>{kp}, f, (R *)nullptr);
+    const Around nb = around(kp, x, y);
+    pull_node_nb<R>(kp, nb, x, y, GlobalAt<S>{kp}, f, (R *)nullptr);
     const R rho = density<R>(f);
-    stencil_S<R>(FieldPsi<R>{kp, psi, x, y}, Sx, Sy);
+    stencil_S<R>(AroundPsi<R>{kp, psi, nb}, Sx, Sy);
     external_force<R>(kp, node, rho, Fex, Fey);
     collide<R>(kp, f, rho, psi[node], Sx, Sy, Fex, Fey, fb, ux, uy);
     store_node<S>(kp, x, y, fb, rho);

@@ -218,6 +218,48 @@ __device__ __forceinline__ bool is_wall_at(const KParams &kp, int x, int y)
     return kp.solid != nullptr && kp.solid[(int64_t)y * kp.nx + x] != 0;
 }
 
+// The 3 x 3 neighbourhood of node (x, y), computed once per node so that everything a
+// kernel gathers from the eight neighbours (the pull, the psi stencil, the wall mask and
+// gathers of the transposed step) shares one set of index arithmetic: the columns x - 1, x, x + 1 and rows y - 1, y, y + 1 wrapped along periodic
+// directions, and bit i set when x + e_i lies inside the lattice.  A neighbour beyond a
+// non-periodic edge takes the node's own column or row, so no index leaves the lattice even
+// where it is not used.  k(i): pitched plane index of x + e_i; n(i): its psi-field index
+// (nx * ny < 2^31).
+struct Around {
+    const KParams &kp;
+    int xc[3], yr[3];
+    unsigned inside;
+    __device__ __forceinline__ int64_t k(int i) const { return (int64_t)yr[ey_(i) + 1] * kp.pitch + xc[ex_(i) + 1]; }
+    __device__ __forceinline__ int64_t n(int i) const { return (int64_t)(yr[ey_(i) + 1] * kp.nx + xc[ex_(i) + 1]); }
+    __device__ __forceinline__ bool in(int i) const { return (inside >> i) & 1u; }
+};
+
+__device__ __forceinline__ Around around(const KParams &kp, int x, int y)
+{
+    Around a{kp};
+    bool okx[3], oky[3];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        int xx = x + d - 1, yy = y + d - 1;
+        okx[d] = oky[d] = true;
+        if (xx < 0 || xx >= kp.nx) {
+            if (kp.periodic_x) xx = xx < 0 ? xx + kp.nx : xx - kp.nx;
+            else okx[d] = false, xx = x;
+        }
+        if (yy < 0 || yy >= kp.ny) {
+            if (kp.periodic_y) yy = yy < 0 ? yy + kp.ny : yy - kp.ny;
+            else oky[d] = false, yy = y;
+        }
+        a.xc[d] = xx;
+        a.yr[d] = yy;
+    }
+    a.inside = 0;
+#pragma unroll
+    for (int i = 0; i < 9; ++i)
+        if (okx[ex_(i) + 1] && oky[ey_(i) + 1]) a.inside |= 1u << i;
+    return a;
+}
+
 // ------------------------------------------------------- global access ------
 // Population i of the source state at pitched index k (or at node (x, y)), decoded.
 template <class S>
@@ -307,6 +349,32 @@ __device__ __forceinline__ void pull_node(const KParams &kp, int x, int y, const
     f[6] = pull_one<R, 6>(kp, x, y, at, mom);
     f[7] = pull_one<R, 7>(kp, x, y, at, mom);
     f[8] = pull_one<R, 8>(kp, x, y, at, mom);
+}
+
+// The same pull with the node's neighbourhood nb (x - e_i = x + e_opp(i)); `at.at_k(k, kk)`
+// reads population k at pitched index kk.
+template <class R, int i, class At>
+__device__ __forceinline__ R pull_one_nb(const KParams &kp, const Around &nb, int x, int y, const At &at, R *mom)
+{
+    if (i == 0) return at.at_k(0, nb.k(0));
+    constexpr int o = opp_(i);
+    if (nb.in(o) && (kp.solid == nullptr || kp.solid[nb.n(o)] == 0)) return at.at_k(i, nb.k(o));
+    return bounce<R, i>(kp, x, y, at, mom);
+}
+
+template <class R, class At>
+__device__ __forceinline__ void pull_node_nb(const KParams &kp, const Around &nb, int x, int y, const At &at,
+                                             R (&f)[9], R *mom)
+{
+    f[0] = pull_one_nb<R, 0>(kp, nb, x, y, at, mom);
+    f[1] = pull_one_nb<R, 1>(kp, nb, x, y, at, mom);
+    f[2] = pull_one_nb<R, 2>(kp, nb, x, y, at, mom);
+    f[3] = pull_one_nb<R, 3>(kp, nb, x, y, at, mom);
+    f[4] = pull_one_nb<R, 4>(kp, nb, x, y, at, mom);
+    f[5] = pull_one_nb<R, 5>(kp, nb, x, y, at, mom);
+    f[6] = pull_one_nb<R, 6>(kp, nb, x, y, at, mom);
+    f[7] = pull_one_nb<R, 7>(kp, nb, x, y, at, mom);
+    f[8] = pull_one_nb<R, 8>(kp, nb, x, y, at, mom);
 }
 
 // FP32 values as one-node lanes of the FP32 formulation (lbm_f32.cuh)
