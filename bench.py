@@ -13,10 +13,10 @@ two-phase channel, annulus and falling-droplet configurations ("geometry").  --i
 times the FP64 CPU oracle instead (bounded sample of the same workload on the host cores).
 """
 import argparse
+import gc
 import json
 import math
 import os
-import gc
 import statistics
 import subprocess
 import sys
