@@ -270,19 +270,20 @@ static bool fused_possible(const lbm_ctx *c)
 }
 
 // LBM_KERNEL_AUTO: the one-pass kernel where it was measured faster than the two-pass one
-// (FP32 on a GB300; the two are close at each threshold).  On small lattices a CTA's serial
-// walk down its rows dominates the one-pass kernel's time and the two-pass kernels, one
-// thread per node, hide latency better: periodic 256^2 7.1 us against 8.8, 512^2 12.4
-// against 10.1; a 256-wide channel with x walls 23.5 against 29.5 (two strips, the second
-// 16 columns wide); 512 x 4096 84 against 57.  Solid bands: 256^2 below, 512^2 19.1 against
-// 19.1 (FP16 26.5 against 21.9), 1024^2 55 against 41, 2048^2 251 against 100.  Interpolated
-// and moving walls, whose per-link work sits on the one-pass kernel's serial path: annulus
-// 1024^2 51 against 58, 2048^2 207 against 195 (FP16 258 against 211).
+// (FP32 on a GB300 unless stated; the two are close at each threshold).  On small lattices a
+// CTA's serial walk down its rows dominates the one-pass kernel's time and the two-pass
+// kernels, one thread per node, hide latency better: periodic 256^2 7.1 us against 8.8,
+// 512^2 12.4 against 10.1; a 256-wide channel with x walls 23.5 against 29.5 (two strips,
+// the second 16 columns wide); 512 x 4096 84 against 57.  Solid bands: 256^2 below, 512^2
+// 17.8 against 19.2 in FP32 but 25.1 against 22.5 in FP16, 1024^2 55 against 41 (before the
+// two-pass kernels shared one neighbourhood computation per node), 2048^2 251 against 100.
+// Interpolated and moving walls, whose per-link work sits on the one-pass kernel's serial
+// path: annulus 1024^2 44 against 58, 2048^2 207 against 195 (FP16 258 against 211).
 static bool auto_prefers_fused(const lbm_ctx *c)
 {
     const int64_t n = (int64_t)c->p.nx * c->p.ny;
     if (c->q || c->wall_u) return n >= (int64_t(1) << 22);
-    if (c->solid) return n >= (int64_t(1) << 18);
+    if (c->solid) return n >= (int64_t(1) << (c->p.precision == LBM_F32 ? 19 : 18));
     return (n >= (int64_t(1) << 18) && c->p.nx >= 512) || n >= (int64_t(1) << 21);
 }
 
