@@ -219,12 +219,13 @@ __device__ __forceinline__ bool is_wall_at(const KParams &kp, int x, int y)
 }
 
 // The 3 x 3 neighbourhood of node (x, y), computed once per node so that everything a
-// kernel gathers from the eight neighbours (the pull, the psi stencil, the wall mask and
-// gathers of the transposed step) shares one set of index arithmetic: the columns x - 1, x, x + 1 and rows y - 1, y, y + 1 wrapped along periodic
-// directions, and bit i set when x + e_i lies inside the lattice.  A neighbour beyond a
-// non-periodic edge takes the node's own column or row, so no index leaves the lattice even
-// where it is not used.  k(i): pitched plane index of x + e_i; n(i): its psi-field index
-// (nx * ny < 2^31).
+// kernel gathers from the eight neighbours (the pull, the psi stencil, the wall mask and the
+// gathers of the transposed step) shares one set of index arithmetic: the columns x - 1, x,
+// x + 1 and rows y - 1, y, y + 1 wrapped along periodic directions, and bit i set when
+// x + e_i lies inside the lattice.  A neighbour beyond a non-periodic edge takes the node's
+// own column or row, so no index leaves the lattice even where it is not used.  k(i): the
+// pitched plane index of x + e_i; n(i): its psi-field index (nx * ny <= 2^31, so it fits an
+// int).
 struct Around {
     const KParams &kp;
     int xc[3], yr[3];
